@@ -1,0 +1,469 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE; see oracle.h).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared [-fopenmp] oracle.c -lm
+ * -ffp-contract=off keeps every a*b+c as two rounded operations, so the op sequence written here is
+ * the one that executes.  OpenMP (when enabled) only splits loops whose iterations are independent
+ * (one agent or one voxel per iteration, no shared accumulator), so results do not depend on the
+ * thread count.
+ *
+ * Only tests, the smoke check and the benchmark's CPU-baseline leg load this file's library.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", SC'11, Sec. 3-4):
+ * ten rounds of the 4-word Philox S-box with multipliers 0xD2511F53, 0xCD9E8D57; between rounds
+ * the 2-word key is bumped by the Weyl constants 0x9E3779B9 and 0xBB67AE85.  One round maps
+ * (c0, c1, c2, c3) to (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0)).
+ * ------------------------------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void orc_philox4x32_10_n(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  for (size_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Uniform grid (paper, "Simulation concepts", environment paragraph: equal boxes, agents assigned by
+ * centre, neighbourhood = own box + 26 surrounding boxes, box size from the largest agent).
+ * Reading R5: centres are quantised to a fixed-point lattice, X = round(x * 2^Q), Q = 20.  With
+ * O = min X, Lq = ceil(L * 2^Q) and box coordinate (X - O) div Lq, two centres closer than R <= L
+ * differ by at most Lq lattice units and so by at most one box per axis: the 27-box search is exact.
+ * ------------------------------------------------------------------------------------------------ */
+#define ORC_Q 20
+
+typedef struct {
+  int64_t O[3];     /* origin, lattice units            */
+  int64_t Lq;       /* box length, lattice units        */
+  int64_t dims[3];  /* boxes per axis                   */
+  int64_t nbox;
+  double R;         /* interaction (neighbour) radius   */
+  double L;         /* requested box length (>= R)      */
+} orc_grid_t;
+
+static int64_t quantise(double v) { return (int64_t)llrint(ldexp(v, ORC_Q)); }
+
+static int grid_setup(size_t n, const double* x, const double* y, const double* z, const float* diam,
+                      double interaction_radius, double box_length, orc_grid_t* G) {
+  if (n == 0) return -1;
+  double dmax = 0.0;
+  for (size_t i = 0; i < n; ++i)
+    if ((double)diam[i] > dmax) dmax = (double)diam[i];
+  G->R = interaction_radius > 0.0 ? interaction_radius : dmax;
+  G->L = box_length > 0.0 ? box_length : G->R;
+  if (!(G->R > 0.0) || G->L < G->R) return -1;
+  G->Lq = (int64_t)ceil(ldexp(G->L, ORC_Q));
+  const double* c[3] = {x, y, z};
+  int64_t nbox = 1;
+  for (int a = 0; a < 3; ++a) {
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    for (size_t i = 0; i < n; ++i) {
+      if (!(fabs(c[a][i]) < 1e9)) return -1; /* also rejects NaN */
+      int64_t X = quantise(c[a][i]);
+      if (X < lo) lo = X;
+      if (X > hi) hi = X;
+    }
+    G->O[a] = lo;
+    G->dims[a] = (hi - lo) / G->Lq + 1;
+    nbox *= G->dims[a];
+    if (nbox > ((int64_t)1 << 32) - 2) return -1;
+  }
+  G->nbox = nbox;
+  return 0;
+}
+
+static void box_coords(const orc_grid_t* G, double x, double y, double z, int64_t b[3]) {
+  b[0] = (quantise(x) - G->O[0]) / G->Lq;
+  b[1] = (quantise(y) - G->O[1]) / G->Lq;
+  b[2] = (quantise(z) - G->O[2]) / G->Lq;
+}
+
+static int64_t box_key(const orc_grid_t* G, const int64_t b[3]) {
+  return b[0] + G->dims[0] * (b[1] + G->dims[1] * b[2]);
+}
+
+static void grid_vector(const orc_grid_t* G, double* g) {
+  if (!g) return;
+  g[0] = (double)G->O[0]; g[1] = (double)G->O[1]; g[2] = (double)G->O[2];
+  g[3] = G->R; g[4] = G->L; g[5] = (double)G->Lq;
+  g[6] = (double)G->dims[0]; g[7] = (double)G->dims[1]; g[8] = (double)G->dims[2];
+  g[9] = (double)G->nbox;
+}
+
+int orc_grid(size_t n, const double* x, const double* y, const double* z, const float* diam,
+             double interaction_radius, double box_length, double* g, uint32_t* box_id) {
+  orc_grid_t G;
+  if (grid_setup(n, x, y, z, diam, interaction_radius, box_length, &G)) return -1;
+  grid_vector(&G, g);
+  for (size_t i = 0; i < n; ++i) {
+    int64_t b[3];
+    box_coords(&G, x[i], y[i], z[i], b);
+    box_id[i] = (uint32_t)box_key(&G, b);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * One mechanics step (agent operation "calculate mechanical forces", paper Sec. "Simulation
+ * concepts"; force law reading R1-R4).  Jacobi: all forces use the positions at step start.
+ * For agent i, neighbours j are visited box by box in ascending box key -- (dz, dy, dx) in
+ * lexicographic order over {-1,0,1}^3 -- and by ascending id inside a box: the canonical order.
+ *   neighbour:  d2 = (dx*dx + dy*dy) + dz*dz  <  R*R            (R1, strict, no sqrt)
+ *   contact:    d = sqrt(d2), delta = (r_i + r_j) - d > 0, d > 0 (R2: coincident centres: no force)
+ *   force:      Rr = r_i r_j / (r_i + r_j);  F = k delta - gamma sqrt(Rr delta)   (R3)
+ *               S_i += (F / d) (x_i - x_j)
+ *   update:     D = dt S_i; if |D| > cap then D *= cap / |D|; x_i += D        (R4)
+ * ------------------------------------------------------------------------------------------------ */
+int orc_mech_step(size_t n, const double* x, const double* y, const double* z, const float* diam,
+                  const orc_mech_params* p, double* nx, double* ny, double* nz, uint32_t* nbr,
+                  uint32_t* box_id, double* g, double* fx, double* fy, double* fz) {
+  orc_grid_t G;
+  if (n == 0) return 0;
+  if (grid_setup(n, x, y, z, diam, p->interaction_radius, p->box_length, &G)) return -1;
+  grid_vector(&G, g);
+
+  /* Canonical order by (box, id): counting sort over ids taken in ascending order. */
+  uint32_t* key = (uint32_t*)malloc(n * sizeof(uint32_t));
+  uint32_t* start = (uint32_t*)calloc((size_t)G.nbox + 1, sizeof(uint32_t));
+  uint32_t* order = (uint32_t*)malloc(n * sizeof(uint32_t));
+  if (!key || !start || !order) {
+    free(key); free(start); free(order);
+    return -2;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    int64_t b[3];
+    box_coords(&G, x[i], y[i], z[i], b);
+    key[i] = (uint32_t)box_key(&G, b);
+    start[key[i] + 1]++;
+  }
+  for (int64_t b = 0; b < G.nbox; ++b) start[b + 1] += start[b];
+  {
+    uint32_t* fill = (uint32_t*)malloc((size_t)G.nbox * sizeof(uint32_t));
+    if (!fill) {
+      free(key); free(start); free(order);
+      return -2;
+    }
+    memcpy(fill, start, (size_t)G.nbox * sizeof(uint32_t));
+    for (size_t i = 0; i < n; ++i) order[fill[key[i]]++] = (uint32_t)i;
+    free(fill);
+  }
+  if (box_id) memcpy(box_id, key, n * sizeof(uint32_t));
+
+  const double R2 = G.R * G.R;
+  const double k = p->k_rep, gam = p->gamma_att, dt = p->dt, cap = p->max_disp;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024)
+#endif
+  for (long long ii = 0; ii < (long long)n; ++ii) {
+    size_t i = (size_t)ii;
+    int64_t b[3];
+    box_coords(&G, x[i], y[i], z[i], b);
+    const double ri = 0.5 * (double)diam[i];
+    double Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    uint32_t cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      int64_t bz = b[2] + dz;
+      if (bz < 0 || bz >= G.dims[2]) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        int64_t by = b[1] + dy;
+        if (by < 0 || by >= G.dims[1]) continue;
+        for (int dxb = -1; dxb <= 1; ++dxb) {
+          int64_t bx = b[0] + dxb;
+          if (bx < 0 || bx >= G.dims[0]) continue;
+          int64_t kb = bx + G.dims[0] * (by + G.dims[1] * bz);
+          for (uint32_t m = start[kb]; m < start[kb + 1]; ++m) {
+            uint32_t j = order[m];
+            if (j == i) continue;
+            double ddx = x[i] - x[j];
+            double ddy = y[i] - y[j];
+            double ddz = z[i] - z[j];
+            double d2 = ddx * ddx + ddy * ddy;
+            d2 = d2 + ddz * ddz;
+            if (d2 < R2) cnt++;
+            double d = sqrt(d2);
+            double rj = 0.5 * (double)diam[j];
+            double delta = (ri + rj) - d;
+            if (delta > 0.0 && d > 0.0) {
+              double Rr = (ri * rj) / (ri + rj);
+              double F = k * delta - gam * sqrt(Rr * delta);
+              double s = F / d;
+              Sx = Sx + s * ddx;
+              Sy = Sy + s * ddy;
+              Sz = Sz + s * ddz;
+            }
+          }
+        }
+      }
+    }
+    if (fx) { fx[i] = Sx; fy[i] = Sy; fz[i] = Sz; }
+    double Dx = dt * Sx, Dy = dt * Sy, Dz = dt * Sz;
+    double norm = Dx * Dx + Dy * Dy;
+    norm = sqrt(norm + Dz * Dz);
+    if (norm > cap) {
+      double f = cap / norm;
+      Dx = Dx * f; Dy = Dy * f; Dz = Dz * f;
+    }
+    nx[i] = x[i] + Dx;
+    ny[i] = y[i] + Dy;
+    nz[i] = z[i] + Dz;
+    nbr[i] = cnt;
+  }
+  free(key); free(start); free(order);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Growth and division (paper Sec. "Simulation concepts": behaviours such as cell division create new
+ * agents; Sec. "Performance": the cell growth and division benchmark).  Reading R7:
+ *   (i)  every agent alive at step start grows: V += dv;
+ *   (ii) agents with V >= vdiv divide, in ascending id; the m-th divider's daughter gets id n + m;
+ *        mother and daughter keep V / 2;
+ *   (iii) every agent's diameter is d = cbrt(6 V / pi) rounded to float;
+ *   (iv) the division axis u comes from Philox key (seed_lo, run), counter (id, step, 2, attempt):
+ *        u_k = w_k * 2^-31 - 1 for k = 0..2, accepted when 2^-20 <= |u|^2 <= 1 (at most 64 tries,
+ *        else u = (0,0,1)), then normalised; the mother moves to x - o u and the daughter to x + o u
+ *        with o = offset_frac * d (d of the halves).
+ * ------------------------------------------------------------------------------------------------ */
+/* pi rounded to double */
+#define ORC_PI 3.141592653589793
+
+static double diameter_of_volume(double v) { return (double)(float)cbrt((v * 6.0) / ORC_PI); }
+
+static void division_axis(uint32_t id, uint32_t step, uint32_t seed_lo, uint32_t run, double u[3]) {
+  const uint32_t key[2] = {seed_lo, run};
+  for (uint32_t attempt = 0; attempt < 64; ++attempt) {
+    const uint32_t ctr[4] = {id, step, 2u, attempt};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double a = ldexp((double)w[0], -31) - 1.0;
+    double b = ldexp((double)w[1], -31) - 1.0;
+    double c = ldexp((double)w[2], -31) - 1.0;
+    double q = a * a + b * b;
+    q = q + c * c;
+    if (q <= 1.0 && q >= ldexp(1.0, -20)) {
+      double len = sqrt(q);
+      u[0] = a / len; u[1] = b / len; u[2] = c / len;
+      return;
+    }
+  }
+  u[0] = 0.0; u[1] = 0.0; u[2] = 1.0;
+}
+
+int orc_grow_divide(size_t n, double* x, double* y, double* z, float* diam, double* vol,
+                    double dv, double vdiv, double offset_frac, uint32_t seed_lo, uint32_t run,
+                    uint32_t step, size_t* n_out) {
+  size_t m = n;
+  for (size_t i = 0; i < n; ++i) {
+    vol[i] = vol[i] + dv;
+    if (vol[i] >= vdiv) {
+      double half = vol[i] * 0.5;
+      double d = diameter_of_volume(half);
+      double u[3];
+      division_axis((uint32_t)i, step, seed_lo, run, u);
+      double o = offset_frac * d;
+      x[m] = x[i] + o * u[0]; y[m] = y[i] + o * u[1]; z[m] = z[i] + o * u[2];
+      x[i] = x[i] - o * u[0]; y[i] = y[i] - o * u[1]; z[i] = z[i] - o * u[2];
+      vol[i] = half; vol[m] = half;
+      diam[i] = (float)d; diam[m] = (float)d;
+      ++m;
+    } else {
+      diam[i] = (float)diameter_of_volume(vol[i]);
+    }
+  }
+  *n_out = m;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Secretion into a substance grid (paper Sec. "Simulation concepts": growth-factor secretion is an
+ * agent behaviour acting on the extracellular substance).  Reading R8: voxel index per axis is
+ * clamp(floor((x - origin) / h), 0, dims - 1); every agent adds q.
+ * ------------------------------------------------------------------------------------------------ */
+static int64_t voxel_of(double v, double o, double h, int64_t n) {
+  double f = floor((v - o) / h);
+  if (!(f >= 0.0)) return 0;
+  if (f >= (double)(n - 1)) return n - 1;
+  return (int64_t)f;
+}
+
+void orc_secrete(size_t n, const double* x, const double* y, const double* z, double* grid,
+                 const int64_t dims[3], const double origin[3], double h, double q) {
+  for (size_t i = 0; i < n; ++i) {
+    int64_t a = voxel_of(x[i], origin[0], h, dims[0]);
+    int64_t b = voxel_of(y[i], origin[1], h, dims[1]);
+    int64_t c = voxel_of(z[i], origin[2], h, dims[2]);
+    grid[a + dims[0] * (b + dims[1] * c)] += q;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Diffusion of an extracellular substance (paper Sec. "Simulation concepts": standalone operation,
+ * once per step).  Reading R9: explicit forward-time centred-space 7-point update,
+ *   u'_v = u_v + lambda * sum_{6 faces} (u_nb - u_v) - mu_dt * u_v,  lambda = D dt / h^2,
+ * zero-flux walls (a missing face neighbour contributes 0).  Mass = sum of u' in FP64, x fastest.
+ * ------------------------------------------------------------------------------------------------ */
+double orc_ftcs(const int64_t dims[3], const double* u, double* out, double lambda, double mu_dt) {
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (long long k = 0; k < (long long)nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        int64_t v = i + nx * (j + ny * (int64_t)k);
+        double c = u[v];
+        double lap = 0.0;
+        if (i > 0) lap = lap + (u[v - 1] - c);
+        if (i < nx - 1) lap = lap + (u[v + 1] - c);
+        if (j > 0) lap = lap + (u[v - nx] - c);
+        if (j < ny - 1) lap = lap + (u[v + nx] - c);
+        if (k > 0) lap = lap + (u[v - nx * ny] - c);
+        if (k < nz - 1) lap = lap + (u[v + nx * ny] - c);
+        out[v] = (c + lambda * lap) - mu_dt * c;
+      }
+  double mass = 0.0;
+  for (int64_t v = 0; v < nx * ny * nz; ++v) mass += out[v];
+  return mass;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * SIR behaviours (paper Sec. "Epidemiology use case"): infection of a susceptible agent with the
+ * infection probability when an infected agent is within the infection radius; recovery of an
+ * infected agent with the recovery probability each step; bounded random movement of every agent.
+ * Reading R10: synchronous step on int32 fixed-point positions in a periodic cube of side L;
+ *   infected-neighbour count uses states and positions at step start, minimum-image distance,
+ *   d^2 < r^2 in 64-bit integers; Philox key (seed_lo, run);
+ *   stream 0, counter (id, step, 0, 0): w0 < thr_inf infects a susceptible with count > 0,
+ *                                       w1 < thr_rec recovers an agent infected at step start;
+ *   stream 1, counter (id, step, 1, 0): move per axis ((w * (2s + 1)) >> 32) - s, wrapped into [0, L).
+ * The grid is nb^3 periodic boxes of side L / nb; an axis with fewer than 3 boxes visits each box once.
+ * ------------------------------------------------------------------------------------------------ */
+static int64_t min_image(int64_t d, int64_t L) {
+  if (d > L / 2) d -= L;
+  else if (d < -(L / 2)) d += L;
+  return d;
+}
+
+int orc_sir_step(size_t n, const int32_t* X, const int32_t* Y, const int32_t* Z, const uint8_t* st,
+                 int32_t L, int32_t nb, int32_t r, int32_t s, uint64_t thr_inf, uint64_t thr_rec,
+                 uint32_t seed_lo, uint32_t run, uint32_t step, int32_t* nX, int32_t* nY,
+                 int32_t* nZ, uint8_t* nst, uint32_t* ninf, uint32_t* box_id, uint32_t counts[3]) {
+  if (L <= 0 || nb <= 0 || L % nb != 0 || L / nb < r || r < 0 || s < 0 || s >= L) return -1;
+  const int64_t Lb = L / nb, nbox = (int64_t)nb * nb * nb;
+  uint32_t* key = (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t));
+  uint32_t* start = (uint32_t*)calloc((size_t)nbox + 1, sizeof(uint32_t));
+  uint32_t* order = (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t));
+  if (!key || !start || !order) {
+    free(key); free(start); free(order);
+    return -2;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (X[i] < 0 || X[i] >= L || Y[i] < 0 || Y[i] >= L || Z[i] < 0 || Z[i] >= L) {
+      free(key); free(start); free(order);
+      return -1;
+    }
+    key[i] = (uint32_t)(X[i] / Lb + nb * (Y[i] / Lb + nb * (Z[i] / Lb)));
+    start[key[i] + 1]++;
+  }
+  for (int64_t b = 0; b < nbox; ++b) start[b + 1] += start[b];
+  {
+    uint32_t* fill = (uint32_t*)malloc((size_t)nbox * sizeof(uint32_t));
+    if (!fill) {
+      free(key); free(start); free(order);
+      return -2;
+    }
+    memcpy(fill, start, (size_t)nbox * sizeof(uint32_t));
+    for (size_t i = 0; i < n; ++i) order[fill[key[i]]++] = (uint32_t)i;
+    free(fill);
+  }
+  if (box_id) memcpy(box_id, key, n * sizeof(uint32_t));
+
+  const uint32_t pkey[2] = {seed_lo, run};
+  const int64_t r2 = (int64_t)r * r;
+  const uint64_t span = 2u * (uint64_t)s + 1u;
+  uint32_t cS = 0, cI = 0, cR = 0;
+  for (size_t i = 0; i < n; ++i) {
+    int64_t b[3] = {X[i] / Lb, Y[i] / Lb, Z[i] / Lb};
+    /* Distinct neighbour box coordinates per axis (periodic). */
+    int64_t nbx[3][3];
+    int cntx[3];
+    for (int a = 0; a < 3; ++a) {
+      cntx[a] = 0;
+      for (int d = -1; d <= 1; ++d) {
+        int64_t c = ((b[a] + d) % nb + nb) % nb;
+        int dup = 0;
+        for (int q = 0; q < cntx[a]; ++q) dup |= (nbx[a][q] == c);
+        if (!dup) nbx[a][cntx[a]++] = c;
+      }
+    }
+    uint32_t infected = 0;
+    for (int qz = 0; qz < cntx[2]; ++qz)
+      for (int qy = 0; qy < cntx[1]; ++qy)
+        for (int qx = 0; qx < cntx[0]; ++qx) {
+          int64_t kb = nbx[0][qx] + nb * (nbx[1][qy] + nb * nbx[2][qz]);
+          for (uint32_t m = start[kb]; m < start[kb + 1]; ++m) {
+            uint32_t j = order[m];
+            if (j == i || st[j] != 1) continue;
+            int64_t dx = min_image((int64_t)X[i] - X[j], L);
+            int64_t dy = min_image((int64_t)Y[i] - Y[j], L);
+            int64_t dz = min_image((int64_t)Z[i] - Z[j], L);
+            if (dx * dx + dy * dy + dz * dz < r2) infected++;
+          }
+        }
+    ninf[i] = infected;
+    uint32_t w[4], mv[4];
+    const uint32_t c0[4] = {(uint32_t)i, step, 0u, 0u};
+    const uint32_t c1[4] = {(uint32_t)i, step, 1u, 0u};
+    orc_philox4x32_10(c0, pkey, w);
+    orc_philox4x32_10(c1, pkey, mv);
+    uint8_t ns = st[i];
+    if (st[i] == 0 && infected > 0 && (uint64_t)w[0] < thr_inf) ns = 1;
+    if (st[i] == 1 && (uint64_t)w[1] < thr_rec) ns = 2;
+    nst[i] = ns;
+    cS += (ns == 0); cI += (ns == 1); cR += (ns == 2);
+    const int32_t* P[3] = {X, Y, Z};
+    int32_t* NP[3] = {nX, nY, nZ};
+    for (int a = 0; a < 3; ++a) {
+      int64_t step_a = (int64_t)(((uint64_t)mv[a] * span) >> 32) - s;
+      int64_t v = (int64_t)P[a][i] + step_a;
+      if (v < 0) v += L;
+      else if (v >= L) v -= L;
+      NP[a][i] = (int32_t)v;
+    }
+  }
+  counts[0] = cS; counts[1] = cI; counts[2] = cR;
+  free(key); free(start); free(order);
+  return 0;
+}

@@ -1,0 +1,198 @@
+"""Seeded synthetic workloads shaped like the paper's use cases.
+
+This module only draws random inputs and holds the parameter recipes of the workloads; it contains
+none of the simulation's arithmetic.  Both the CUDA path and the FP64 oracle are fed from here.
+
+Workloads (BioDynaMo, arXiv 2006.06775; Sec. "Performance" names the cell growth and division
+benchmark, Sec. "Oncology use case" the tumour spheroid, Sec. "Epidemiology use case" the SIR model):
+
+  plain_mechanics     4096 spheres, centres U[0,160)^3 um, diameters U[8,12] um, seed 0, FP64,
+                      repulsion 2.0, attraction 1.0, dt 0.01, displacement cap 3 um, 10 steps.
+  spheroid            512 cells on an 8^3 lattice (spacing 12 um, centred on the origin,
+                      jitter U[-0.5,0.5] um per axis), diameter 10 um, seed 1; growth 100 um^3 per
+                      step, division at diameter 14 um; secretion 1.0 per cell per step into a 128^3
+                      FP32 grid (voxel 10 um, origin -640 um, D 0.4, decay 0.01, dt 1, closed walls).
+  large_mechanics     10^8 spheres at 0.3 volume fraction (cube side 5662 um), diameters U[8,12],
+                      seed 2; a 512^3 FP32 grid spanning the cube co-stepped (D 0.4, decay 0.01, dt 1)
+                      from a seeded smooth random field.
+  sir_ensemble        256 runs x 20,000 persons in a 1000 um periodic cube, 2% infected, step 5 um,
+                      infection radius 6 um, p_inf ~ U[0.1,0.4], p_rec ~ U[0.01,0.03] per run, seed 3.
+  served_stream       Poisson arrivals (200/s), log-uniform sizes 1e3..1e6 agents, 50..500 steps,
+                      70% mechanics / 30% SIR, seed 4.
+"""
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def rng(seed: int, stream: int = 0) -> np.random.Generator:
+    """Counter-based Philox bit generator keyed by (seed, stream)."""
+    return np.random.Generator(np.random.Philox(key=(int(stream) << 32) | int(seed)))
+
+
+# ------------------------------------------------------------------------------------------------
+# Mechanics populations
+# ------------------------------------------------------------------------------------------------
+MECH_DEFAULTS = dict(kind="mechanics", dt=0.01, repulsion=2.0, attraction=1.0,
+                     max_displacement=3.0, interaction_radius=0.0, box_length=0.0)
+
+VOLUME_FRACTION_LARGE = 0.3
+MEAN_SPHERE_VOLUME_8_12 = math.pi / 6.0 * (12.0 ** 4 - 8.0 ** 4) / (4.0 * 4.0)  # E[d^3] = 544.5*6/pi
+
+
+def uniform_spheres(n: int, side: float, seed: int, stream: int = 0, dmin=8.0, dmax=12.0):
+    """n centres uniform in [0, side)^3 and diameters uniform in [dmin, dmax] (float32)."""
+    g = rng(seed, stream)
+    x = g.uniform(0.0, side, n)
+    y = g.uniform(0.0, side, n)
+    z = g.uniform(0.0, side, n)
+    d = g.uniform(dmin, dmax, n).astype(np.float32)
+    return x, y, z, d
+
+
+def plain_mechanics(n: int = 4096, side: float = 160.0, seed: int = 0):
+    """Plain-mechanics population (default: 4096 agents in a 160 um cube)."""
+    x, y, z, d = uniform_spheres(n, side, seed)
+    params = dict(MECH_DEFAULTS, precision="fp64", seed=seed)
+    return params, dict(x=x, y=y, z=z, diameter=d)
+
+
+def large_side(n: int, volume_fraction: float = VOLUME_FRACTION_LARGE) -> float:
+    """Cube side that puts n spheres (diameters U[8,12]) at the given volume fraction."""
+    return (n * MEAN_SPHERE_VOLUME_8_12 / volume_fraction) ** (1.0 / 3.0)
+
+
+def large_mechanics(n: int = 100_000_000, seed: int = 2, grid_n: int = 512, with_grid=True):
+    """Large mechanics + diffusion population at 0.3 volume fraction (side 5662 um at 10^8)."""
+    side = large_side(n)
+    x, y, z, d = uniform_spheres(n, side, seed)
+    params = dict(MECH_DEFAULTS, precision="mixed", seed=seed)
+    inputs = dict(x=x, y=y, z=z, diameter=d, side=side)
+    if with_grid and grid_n:
+        params.update(diffusion_enabled=1, grid_n=(grid_n, grid_n, grid_n),
+                      grid_origin=(0.0, 0.0, 0.0), voxel=side / grid_n, diffusion_coeff=0.4,
+                      decay=0.01, dt_diffusion=1.0, secretion=0.0)
+        inputs["grid"] = smooth_field(grid_n, seed)
+    return params, inputs
+
+
+def smooth_field(n: int, seed: int, modes: int = 6) -> np.ndarray:
+    """Seeded smooth positive random field of shape (n, n, n), float32: a sum of a few low-frequency
+    separable cosines around 1.0."""
+    g = rng(seed, 7)
+    t = (np.arange(n, dtype=np.float64) + 0.5) / n
+    field = np.ones((n, n, n), np.float32)
+    for _ in range(modes):
+        kx, ky, kz = g.integers(1, 5, 3)
+        px, py, pz = g.uniform(0, 2 * math.pi, 3)
+        a = g.uniform(0.05, 0.15)
+        fx = np.cos(2 * math.pi * kx * t + px).astype(np.float32)
+        fy = np.cos(2 * math.pi * ky * t + py).astype(np.float32)
+        fz = np.cos(2 * math.pi * kz * t + pz).astype(np.float32)
+        field += np.float32(a) * fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    return field
+
+
+def spheroid(seed: int = 1, lattice: int = 8, spacing: float = 12.0, diameter: float = 10.0,
+             grid_n: int = 128):
+    """Tumour-spheroid start: lattice^3 cells centred on the origin with +-0.5 um jitter."""
+    g = rng(seed)
+    idx = np.arange(lattice, dtype=np.float64) - (lattice - 1) / 2.0
+    zz, yy, xx = np.meshgrid(idx, idx, idx, indexing="ij")
+    n = lattice ** 3
+    x = xx.reshape(-1) * spacing + g.uniform(-0.5, 0.5, n)
+    y = yy.reshape(-1) * spacing + g.uniform(-0.5, 0.5, n)
+    z = zz.reshape(-1) * spacing + g.uniform(-0.5, 0.5, n)
+    d = np.full(n, diameter, np.float32)
+    division_diameter = 14.0
+    params = dict(MECH_DEFAULTS, precision="mixed", seed=seed, growth_enabled=1,
+                  growth_volume=100.0,
+                  division_volume=math.pi / 6.0 * division_diameter ** 3,
+                  division_offset_frac=0.25, interaction_radius=division_diameter,
+                  diffusion_enabled=1, grid_n=(grid_n, grid_n, grid_n),
+                  grid_origin=(-640.0, -640.0, -640.0), voxel=10.0, diffusion_coeff=0.4,
+                  decay=0.01, dt_diffusion=1.0, secretion=1.0)
+    return params, dict(x=x, y=y, z=z, diameter=d)
+
+
+# ------------------------------------------------------------------------------------------------
+# SIR ensemble
+# ------------------------------------------------------------------------------------------------
+SIR_UNIT = 1.0 / 1024.0  # positions are drawn on the 2^-10 um lattice the SIR model runs on
+
+
+def sir_run(n: int, seed: int, run: int, domain: float = 1000.0, infected_frac: float = 0.02):
+    """One SIR population: lattice-exact uniform positions, the first floor(f n) agents of a seeded
+    permutation infected.  Returns positions in um and the state vector (0 S, 1 I, 2 R)."""
+    g = rng(seed, 1000 + run)
+    units = int(round(domain / SIR_UNIT))
+    X = g.integers(0, units, n)
+    Y = g.integers(0, units, n)
+    Z = g.integers(0, units, n)
+    state = np.zeros(n, np.uint8)
+    state[g.permutation(n)[: int(math.floor(infected_frac * n))]] = 1
+    return X * SIR_UNIT, Y * SIR_UNIT, Z * SIR_UNIT, state
+
+
+def sir_ensemble(runs: int = 256, n: int = 20_000, seed: int = 3, domain: float = 1000.0,
+                 boxes: int = 40):
+    """Per-run parameters and populations of the batched SIR ensemble."""
+    g = rng(seed, 999)
+    p_inf = g.uniform(0.1, 0.4, runs)
+    p_rec = g.uniform(0.01, 0.03, runs)
+    out = []
+    for r in range(runs):
+        params = dict(kind="sir", seed=seed, run_id=r, sir_domain=domain, sir_radius=6.0,
+                      sir_step=5.0, sir_boxes=boxes, p_infect=float(p_inf[r]),
+                      p_recover=float(p_rec[r]))
+        x, y, z, st = sir_run(n, seed, r, domain)
+        out.append((params, dict(x=x, y=y, z=z, sir_state=st)))
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# Served request stream
+# ------------------------------------------------------------------------------------------------
+@dataclass
+class Request:
+    rid: int
+    arrival: float   # seconds after stream start
+    kind: str        # "mechanics" | "sir"
+    n: int
+    steps: int
+    seed: int
+
+
+def request_stream(count: int = 2000, rate: float = 200.0, seed: int = 4, nmin=1e3, nmax=1e6,
+                   smin=50, smax=500, mech_frac=0.7):
+    """Poisson arrivals with log-uniform sizes and uniform step counts."""
+    g = rng(seed, 5)
+    gaps = g.exponential(1.0 / rate, count)
+    t = np.cumsum(gaps) - gaps[0]
+    sizes = np.exp(g.uniform(math.log(nmin), math.log(nmax), count)).astype(np.int64)
+    steps = g.integers(smin, smax + 1, count)
+    kinds = np.where(g.uniform(0, 1, count) < mech_frac, "mechanics", "sir")
+    return [Request(i, float(t[i]), str(kinds[i]), int(sizes[i]), int(steps[i]), seed * 100000 + i)
+            for i in range(count)]
+
+
+def served_mechanics(n: int, seed: int, density: float = 4096 / 160.0 ** 3):
+    """A served mechanics request: plain-mechanics density, cube side scaled with n^(1/3)."""
+    side = (n / density) ** (1.0 / 3.0)
+    x, y, z, d = uniform_spheres(n, side, seed)
+    params = dict(MECH_DEFAULTS, precision="mixed", seed=seed)
+    return params, dict(x=x, y=y, z=z, diameter=d)
+
+
+def served_sir(n: int, seed: int, density: float = 20_000 / 1000.0 ** 3, boxes_per_side=None):
+    """A served SIR request at the ensemble's density (domain scaled with n^(1/3), rounded to a whole
+    number of um so the box count divides the lattice)."""
+    domain = float(max(20, int(round((n / density) ** (1.0 / 3.0)))))
+    g = rng(seed, 11)
+    p_inf = float(g.uniform(0.1, 0.4))
+    p_rec = float(g.uniform(0.01, 0.03))
+    x, y, z, st = sir_run(n, seed, 0, domain)
+    params = dict(kind="sir", seed=seed, run_id=0, sir_domain=domain, sir_radius=6.0, sir_step=5.0,
+                  sir_boxes=boxes_per_side or 0, p_infect=p_inf, p_recover=p_rec)
+    return params, dict(x=x, y=y, z=z, sir_state=st)
