@@ -1,0 +1,324 @@
+"""Benchmark of the mechanics hot path: agent-steps/s on the large mechanics + diffusion workload
+(10^8 spheres at 0.3 volume fraction, 512^3 FP32 substance grid co-stepped, FP32 forces / FP64
+positions), one JSON line on stdout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--agents N]
+
+A step is one pass of the whole hot path: grid rebuild (bounds, box ids + histogram, scan, scatter,
+canonical gather), force + capped update, and one FTCS diffusion step with its FP64 mass total.
+Timed on the device with CUDA events on the library's stream; inputs (12+ GB of agent state) are far
+larger than L2.  Under torchrun each rank runs an independent replica (the path is not sharded across
+GPUs), value = agents x steps x ranks / max-over-ranks time.
+
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2006_06775_gb300 import synth  # noqa: E402
+
+WORKLOAD = "large_mechanics: 1e8 spheres (d~U[8,12] um, 0.3 volume fraction, 5662 um cube) + 512^3 FP32 FTCS grid"
+METRIC = "agent-steps/s"
+
+# Algorithmic bytes (compulsory traffic: every input read once, every output written once) per agent
+# of each kernel of the mixed-precision step; the box-array terms scale with boxes per agent (B).
+KERNEL_BYTES = {
+    "key_hist": lambda B: 24 + 8 + 8 * B,        # FP64 centres in; key + rank out; histogram r/w
+    "scan_box": lambda B: 12 * B,                # counts in, starts out, counts cleared
+    "scatter": lambda B: 12 + 4 + 4 * B,         # key + rank in, starts, perm out
+    "gather": lambda B: 44 + 48 + 4 * B,         # perm, key, payload (32) in; payload + skey + p4 out
+    "force_mixed": lambda B: 44 + 28 + 4 * B,    # p4, FP64 centre, skey in; centre + count out
+}
+STEP_BYTES_PER_AGENT = lambda B: 4 * 32 + 8 * B  # rebuild + force + update, agent state S = 32 B
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_uuid=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if gpu_uuid:
+            cmd += ["-i", gpu_uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for name, v in zip(names, r[4:8]):
+                    if v.strip() == "Active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(n, seed):
+    params, inp = synth.large_mechanics(n=n, seed=seed, grid_side=synth.large_side(n))
+    return params, inp
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------------
+def oracle_sample_rate(n_sample=2_000_000, steps=1, seed=2):
+    import oracle
+    frac = n_sample / 1e8
+    gn = max(8, int(round(512 * frac ** (1.0 / 3.0))))
+    params, inp = synth.large_mechanics(n=n_sample, seed=seed, grid_n=gn)
+    sim = oracle.OracleSim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    sim.set_grid(inp["grid"])
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample * steps / dt, "unit": METRIC, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d step(s) of %d agents at the same density with a %d^3 grid (same voxel "
+                      "size), FP64, OpenMP over agents; %.1f s" % (steps, n_sample, gn, dt),
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_sample = args.cpu_sample
+    for _ in range(args.warmup):
+        oracle_sample_rate(n_sample, 1)
+    rates, secs = [], 0.0
+    for _ in range(args.steps):
+        r = oracle_sample_rate(n_sample, 1)
+        rates.append(r["value"])
+        secs += r["seconds"]
+    value = n_sample * args.steps / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "agents": int(1e8), "grid": 512,
+                       "sample_agents": n_sample},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": r["cores"],
+                             "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2006_06775_gb300 import bdm
+    import paper_2006_06775_gb300.build as libbuild
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    libbuild.build()
+    bdm.load(build_if_missing=False)
+    n = args.agents
+    params, inp = make_workload(n, seed=2 + rank)
+    stream = torch.cuda.Stream()
+    sim = bdm.Sim(params, stream=stream)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    sim.set_grid(inp["grid"])
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    st0 = sim.get_state(fields=())
+    nbox = int(np.prod(st0["grid_dims"]))
+    boxes_per_agent = nbox / n
+
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+    sim.profile(True)
+    launches0 = bdm.bdm_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = bdm.bdm_launch_count() - launches0
+    ktimes = sim.kernel_times()
+    sim.profile(False)
+    clk = clocks.stop()
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = n * args.steps * world / (elapsed_ms * 1e-3)
+    ms_per_step = elapsed_ms / args.steps
+
+    peak, peak_kind = load_peaks()
+    # dominant kernel and its roofline
+    per_launch = {k: v[1] / max(v[0], 1) for k, v in ktimes.items()}
+    share = {k: v[1] for k, v in ktimes.items()}
+    dom = max((k for k in share if k in KERNEL_BYTES), key=lambda k: share[k])
+    alg_bytes = KERNEL_BYTES[dom](boxes_per_agent) * n
+    achieved = alg_bytes / (per_launch[dom] * 1e-3) / 1e9
+    mech_ms = sum(v[1] for k, v in ktimes.items() if k != "ftcs") / args.steps
+    step_bytes = STEP_BYTES_PER_AGENT(boxes_per_agent) * n + 8.0 * 512 ** 3
+    step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample_rate(args.cpu_sample, 1)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 forces, f64 positions",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "agents": n, "grid": 512, "precision": "mixed",
+                       "boxes_per_agent": round(boxes_per_agent, 4),
+                       "cache": "inputs larger than L2 (agent state ~12 GB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "alg_bytes_per_agent": KERNEL_BYTES[dom](boxes_per_agent)},
+            "step_roofline": {"bytes_per_agent_step": STEP_BYTES_PER_AGENT(boxes_per_agent),
+                              "diffusion_bytes_per_step": 8 * 512 ** 3,
+                              "achieved": step_achieved, "peak": peak, "unit": "GB/s",
+                              "frac": step_achieved / peak, "mechanics_ms_per_step": mech_ms},
+            "kernels_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(sim, inp, n, steps, stream):
+    """End to end through the C ABI: pinned host inputs -> add agents + grid -> `steps` steps ->
+    positions and mass back to pinned host memory, per job."""
+    import torch
+    from paper_2006_06775_gb300 import bdm
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    hx, hy, hz = pinned(inp["x"]), pinned(inp["y"]), pinned(inp["z"])
+    hd = pinned(inp["diameter"])
+    hg = pinned(inp["grid"].reshape(-1))
+    outs = {a: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for a in ("x", "y", "z")}
+    h2d = n * (3 * 8 + 4) + hg.numel() * 4
+    d2h = n * 3 * 8 + 8
+    times = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.reset()
+        sim.add_agents(hx.numpy(), hy.numpy(), hz.numpy(), hd.numpy())
+        sim.set_grid(hg.numpy())
+        sim.step(steps)
+        st = sim.get_state(fields=("x", "y", "z"), out=outs)
+        times.append(time.perf_counter() - t0)
+        assert st["n"] == n
+    t = min(times)
+    return {"value": n * steps / t, "unit": METRIC, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "steps_per_job": steps,
+            "job_seconds": t}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--agents", type=int, default=100_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * bdm.h -- C ABI of libbdm.so, the GB300 (sm_103a) agent-mechanics hot path of the BioDynaMo
+ * simulation loop (Breitwieser et al., arXiv 2006.06775).
+ *
+ * The calls follow the paper's statement of a simulation (Sec. "Simulation concepts", Fig. 1D):
+ * initialisation (bdm_create, bdm_add_agents, bdm_set_grid: place agents, set attributes, choose
+ * behaviours), execution (bdm_step: agent operations -- behaviours and mechanical forces -- for every
+ * agent each step, plus the standalone diffusion operation; bdm_diffusion_step: the standalone
+ * operation alone), and read-out (bdm_get_state, including the SIR counting operation of Sec.
+ * "Epidemiology use case").
+ *
+ * Conventions
+ *  - Every function returns a bdm_status; 0 is success, negative is an error. bdm_last_error gives
+ *    a message for the handle (thread-unsafe: one handle per host thread).
+ *  - Ownership: the library owns the opaque handles and all device memory they hold. The caller owns
+ *    every buffer it passes. Input pointers in this header are HOST pointers, copied in before the
+ *    call returns; output pointers are HOST pointers filled before the call returns.
+ *  - Ordering: state crosses the boundary in agent-id order (ids 0..n-1 in insertion order, then
+ *    division daughters). Internally agents live in box order on the device.
+ *  - Streams: work is enqueued on bdm_params.stream (a cudaStream_t, NULL = the legacy default
+ *    stream) and is asynchronous, except bdm_get_state, which synchronises that stream. A device
+ *    error word (grid overflow, capacity overflow, a bounded wait that timed out) is checked at the
+ *    next synchronising call and returned as BDM_ESTATE / BDM_ENOMEM / BDM_ETIMEOUT; the handle
+ *    then refuses further steps.
+ *  - Memory: if alloc/free are given, every device allocation goes through them (for example the
+ *    PyTorch caching allocator); otherwise cudaMalloc/cudaFree. All buffers are sized at creation
+ *    (capacity, box_capacity); no step allocates.
+ */
+#ifndef BDM_H
+#define BDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BDM_ABI_VERSION 1
+
+typedef enum {
+  BDM_OK = 0,
+  BDM_EINVAL = -1,   /* invalid argument or parameter                                   */
+  BDM_ENOMEM = -2,   /* allocation failed, or capacity / box capacity exceeded           */
+  BDM_ECUDA = -3,    /* a CUDA runtime call failed (message names it)                    */
+  BDM_ESTATE = -4,   /* a kernel flagged an inconsistent state; the handle is poisoned   */
+  BDM_ETIMEOUT = -5, /* a bounded device-side wait ran out                               */
+  BDM_EBUDGET = -6   /* request exceeds a memory budget                                  */
+} bdm_status;
+
+enum { BDM_MECHANICS = 0, BDM_SIR = 1 };
+enum { BDM_FP64 = 0, BDM_MIXED = 1 };
+
+/* Simulation parameters.  Zero-initialise, then set struct_size = sizeof(bdm_params). */
+typedef struct bdm_params {
+  uint32_t struct_size;          /* = sizeof(bdm_params) (ABI check)                             */
+  int32_t kind;                  /* BDM_MECHANICS or BDM_SIR                                      */
+  int32_t precision;             /* BDM_FP64: all-FP64 force/update; BDM_MIXED: FP32 forces from
+                                    box-relative offsets, FP64 positions                         */
+  int32_t record_diagnostics;    /* reserved, 0                                                   */
+  /* Mechanics (readings R1-R6: neighbour radius, force law, capped update, grid). */
+  double dt;                     /* displacement = dt * summed force                               */
+  double repulsion;              /* k in F = k delta - gamma sqrt(rho delta)                       */
+  double attraction;             /* gamma                                                          */
+  double max_displacement;       /* cap on |displacement| per step                                 */
+  double interaction_radius;     /* neighbour radius R; 0 = largest diameter, every step          */
+  double box_length;             /* grid box L >= R; 0 = R                                         */
+  /* Growth and division (reading R7). */
+  int32_t growth_enabled;
+  int32_t reserved1;
+  double growth_volume;          /* volume added per step                                          */
+  double division_volume;        /* divide when volume >= this                                     */
+  double division_offset_frac;   /* mother/daughter offset = frac * daughter diameter             */
+  /* Substance grid: secretion (R8) and FTCS diffusion (R9). */
+  int32_t diffusion_enabled;     /* co-step one FTCS step after mechanics in bdm_step              */
+  int32_t grid_n[3];             /* voxels per axis (x, y, z); layout x fastest                    */
+  double grid_origin[3];
+  double voxel;                  /* h                                                              */
+  double diffusion_coeff;        /* D                                                              */
+  double decay;                  /* mu                                                             */
+  double dt_diffusion;           /* dt of one FTCS step                                            */
+  double secretion;              /* amount each agent adds per step; 0 = none                      */
+  /* SIR (reading R10); lengths in um, run on a 2^-10 um int32 lattice. */
+  double sir_domain;             /* periodic cube side L                                           */
+  double sir_radius;             /* infection radius r                                             */
+  double sir_step;               /* per-axis move bound s                                          */
+  double p_infect;
+  double p_recover;
+  int32_t sir_boxes;             /* boxes per axis nb (L / nb >= r, nb divides the lattice side);
+                                    0 = largest admissible box count <= L / r                    */
+  int32_t reserved2;
+  /* Random streams: Philox4x32-10 key = (seed low 32 bits, run_id). */
+  uint64_t seed;
+  uint32_t run_id;
+  uint32_t reserved3;
+  /* Capacities. */
+  uint64_t capacity;             /* max agents (growth appends up to it); 0 = agents of the first
+                                    bdm_add_agents call                                           */
+  uint64_t box_capacity;         /* max grid boxes; 0 = automatic (4 x initial + margin)           */
+  /* Device plumbing. */
+  void* stream;                  /* cudaStream_t                                                   */
+  void* (*alloc)(size_t bytes, void* user); /* optional device allocator                         */
+  void (*free)(void* ptr, void* user);
+  void* alloc_user;
+} bdm_params;
+
+/* Read-out of one simulation.  Set struct_size; every pointer may be NULL (field skipped); buffers
+ * must hold at least `n` entries (query n first with all pointers NULL), grid prod(grid_n). */
+typedef struct bdm_state {
+  uint32_t struct_size;          /* = sizeof(bdm_state)                                            */
+  uint32_t reserved0;
+  uint64_t n;                    /* out: number of agents                                          */
+  uint64_t step;                 /* out: steps completed                                           */
+  double* x;                     /* positions, um                                                   */
+  double* y;
+  double* z;
+  float* diameter;               /* mechanics                                                      */
+  double* volume;                /* mechanics with growth                                          */
+  uint8_t* sir_state;            /* SIR: 0 susceptible, 1 infected, 2 recovered                    */
+  uint32_t* neighbour_count;     /* last step: mechanics -> agents within R; SIR -> infected
+                                    agents within r (both at step start)                          */
+  uint32_t* box_id;              /* last step's grid assignment of each agent                      */
+  float* grid;                   /* substance grid, x fastest                                      */
+  double mass_total;             /* out: FP64 total of the substance grid                          */
+  uint32_t sir_counts[3];        /* out: S, I, R after the last step                               */
+  uint32_t reserved1;
+  int64_t grid_origin_q[3];      /* out: last grid origin, 2^-20 um lattice units (mechanics)      */
+  int64_t grid_box_q;            /* out: box length, lattice units                                 */
+  int64_t grid_dims[3];          /* out: boxes per axis                                            */
+} bdm_state;
+
+typedef struct bdm_sim bdm_sim;
+
+/* Create a simulation handle.  Validates p (BDM_EINVAL), allocates device state for p->capacity
+ * agents (or defers to the first bdm_add_agents when 0) and p->box_capacity boxes. */
+int bdm_create(const bdm_params* p, bdm_sim** out);
+
+/* Append n agents (ids continue from the current count).  x, y, z: host arrays of n doubles (um).
+ * diameter: n floats (mechanics; NULL for SIR).  volume: n doubles or NULL (then pi/6 d^3).
+ * sir_state: n bytes or NULL (all susceptible).  SIR positions must lie in [0, sir_domain) and are
+ * rounded to the 2^-10 um lattice.  BDM_ENOMEM beyond capacity. */
+int bdm_add_agents(bdm_sim* s, size_t n, const double* x, const double* y, const double* z,
+                   const float* diameter, const double* volume, const uint8_t* sir_state);
+
+/* Replace the substance grid with prod(grid_n) host floats (x fastest). */
+int bdm_set_grid(bdm_sim* s, const float* values);
+
+/* Set the step counter (Philox counters are keyed by it); used to resume from a saved state. */
+int bdm_set_step(bdm_sim* s, uint64_t step);
+
+/* Remove all agents and zero the step counter, keeping every allocation. */
+int bdm_reset(bdm_sim* s);
+
+/* Advance n steps (reading R11 order).  Asynchronous; n-step sequences are captured once into a
+ * CUDA graph and replayed. */
+int bdm_step(bdm_sim* s, int n);
+
+/* Advance the substance grid alone by n FTCS steps (standalone operation). */
+int bdm_diffusion_step(bdm_sim* s, int n);
+
+/* Copy the state to caller buffers in agent-id order.  Synchronises the stream. */
+int bdm_get_state(bdm_sim* s, bdm_state* st);
+
+void bdm_destroy(bdm_sim* s);
+const char* bdm_last_error(const bdm_sim* s);
+
+/* ---- Profiling: per-kernel CUDA-event timing on the simulation's stream ---------------------- */
+typedef struct bdm_kernel_time {
+  char name[32];
+  uint64_t launches;
+  double total_ms;
+} bdm_kernel_time;
+
+/* enable != 0: record an event pair around every kernel the handle launches (no graph replay while
+ * enabled: steps are issued kernel by kernel). */
+int bdm_profile(bdm_sim* s, int enable);
+/* Fill up to max entries (synchronises); returns the number of distinct kernels in *count. */
+int bdm_kernel_times(bdm_sim* s, bdm_kernel_time* out, int max, int* count);
+/* Kernels this process has launched through libbdm (graph replays count each node). */
+uint64_t bdm_launch_count(void);
+/* Library version string. */
+const char* bdm_version(void);
+
+/* ---- Utility ----------------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind division axes and the SIR
+ * behaviours, evaluated by the library's device code.  ctr: n x 4 words, key: n x 2 words, out:
+ * n x 4 words, all HOST arrays (row-major).  Allocates temporary device memory.  Used to check the
+ * device generator against independent implementations. */
+int bdm_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

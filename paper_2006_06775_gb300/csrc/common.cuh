@@ -1,0 +1,230 @@
+// common.cuh -- shared definitions of the libbdm CUDA kernels (sm_103a).
+//
+// Everything here is device plumbing for the hot path of the BioDynaMo step (arXiv 2006.06775,
+// Sec. "Simulation concepts"): the device-resident grid description, error bits, exact integer
+// helpers for the grid lattice (reading R5), and a Philox4x32-10 generator written from its
+// published definition (Salmon et al., SC'11).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bdm.h"
+
+namespace bdm {
+
+constexpr int kQ = 20;                        // grid lattice: 2^-20 um (reading R5)
+constexpr double kQScale = 1048576.0;         // 2^20
+constexpr float kQInv = 1.0f / 1048576.0f;    // 2^-20, exact
+constexpr int kBlock = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kBlock * kScanItems; // 4096 items per scan tile
+constexpr unsigned kSpinLimit = 1u << 22;      // bounded waits: ~0.5 s with 100 ns sleeps
+
+enum ErrBit : unsigned {
+  ERR_GRID_OVERFLOW = 1u,   // grid needs more boxes than box_capacity
+  ERR_CAPACITY = 2u,        // division would exceed agent capacity
+  ERR_TIMEOUT = 4u,         // a bounded spin-wait gave up
+  ERR_RADIUS = 8u,          // box length below interaction radius / bad extent
+  ERR_BOUNDS = 16u,         // an index check failed (never expected)
+};
+
+// Device-resident description of the current step's grid and counters.  Written by the finalize
+// kernel, read by every kernel of the step, so that a step needs no host round trip and a whole
+// n-step sequence can be captured in one CUDA graph.
+struct DevGrid {
+  unsigned long long acc_min[3];  // order-preserving encodings of the per-axis minimum centre
+  unsigned long long acc_max[3];
+  unsigned acc_maxdiam;           // float bits of the largest diameter (diameters are positive)
+  unsigned n;                     // agents
+  long long O[3];                 // origin, lattice units
+  long long Lq;                   // box length, lattice units
+  int dims[3];                    // boxes per axis
+  unsigned nbox;
+  unsigned nbox1;                 // nbox + 1: items of the box scan
+  unsigned ndiv1;                 // n_old + 1: items of the division scan
+  double R;                       // interaction radius (um)
+  double R2;                      // R * R
+  float Lf;                       // box length in um (float of Lq * 2^-20)
+  float R2f;                      // float(R2)
+  float R2lo, R2hi;               // FP32 band around R2 inside which the FP64 test decides
+  float invLq;                    // float(1 / Lq): estimate for the box division
+  unsigned scan_ctr[2];           // dynamic tile counters of the two scans
+  unsigned err;                   // ErrBit flags
+  unsigned sir_counts[3];         // S, I, R after the last SIR step
+  unsigned long long step;        // steps completed (Philox counters)
+  double mass;                    // FP64 substance total after the last diffusion step
+};
+
+struct MechConsts {               // per-simulation constants passed by value
+  double dt, k, gamma, cap;
+  float dtf, kf, gammaf, capf;
+  double interaction_radius, box_length;
+  unsigned box_capacity, capacity;
+};
+
+// ---- exact helpers -------------------------------------------------------------------------
+
+// Order-preserving map of a (non-NaN) double to uint64: a < b  <=>  enc(a) < enc(b).
+__device__ __forceinline__ unsigned long long enc_double(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dec_double(unsigned long long e) {
+  unsigned long long b = (e >> 63) ? (e & 0x7FFFFFFFFFFFFFFFull) : ~e;
+  return __longlong_as_double((long long)b);
+}
+
+// round(v * 2^20) with ties to even, using integer operations on the IEEE-754 bits (no FP64 pipe).
+// Valid for |v| < 2^40 um; the result equals llrint(ldexp(v, 20)).
+__device__ __forceinline__ long long quantise(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;                                    // zero / subnormal -> 0
+  unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  int sh = e - 1075 + kQ;                                  // v * 2^20 = m * 2^sh
+  unsigned long long q;
+  if (sh >= 0) {
+    q = m << sh;                                           // sh <= 8 for |v| < 2^40
+  } else if (sh < -54) {
+    q = 0;                                                 // |v * 2^20| < 1/2
+  } else {
+    int s = -sh;                                           // 1..54
+    unsigned long long rem = m & ((1ull << s) - 1ull);
+    unsigned long long half = 1ull << (s - 1);
+    q = m >> s;
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// floor(D / Lq) for 0 <= D < 2^62, 0 < Lq < 2^40: a float estimate corrected by exact products.
+__device__ __forceinline__ int box_div(long long D, long long Lq, float invLq) {
+  float df = (float)(D >> 20) * 1048576.0f + (float)(D & 0xFFFFF);
+  long long q = (long long)(int)(df * invLq);
+  if (q < 0) q = 0;
+  while (q > 0 && q * Lq > D) --q;
+  while ((q + 1) * Lq <= D) ++q;
+  return (int)q;
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------------------------
+// Round: (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)) with
+// M0 = 0xD2511F53, M1 = 0xCD9E8D57; the key is bumped by (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// ---- block reductions -------------------------------------------------------------------------
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_reduce(T v, Op op) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block-wide bounds commit: min/max of order-preserving centre encodings and the largest diameter
+// bits, one atomic per quantity per block.  Every thread of the block must call it.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void block_commit_bounds(unsigned long long mn[3], unsigned long long mx[3],
+                                    unsigned md, DevGrid* g) {
+  __shared__ unsigned long long s_mn[3][kBlock / 32], s_mx[3][kBlock / 32];
+  __shared__ unsigned s_md[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto umin = [](unsigned long long a, unsigned long long b) { return a < b ? a : b; };
+  auto umax = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
+  for (int a = 0; a < 3; ++a) {
+    mn[a] = warp_reduce(mn[a], umin);
+    mx[a] = warp_reduce(mx[a], umax);
+  }
+  md = warp_reduce(md, [](unsigned a, unsigned b) { return a > b ? a : b; });
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) {
+      s_mn[a][warp] = mn[a];
+      s_mx[a][warp] = mx[a];
+    }
+    s_md[warp] = md;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kBlock / 32; ++w) {
+      for (int a = 0; a < 3; ++a) {
+        s_mn[a][0] = umin(s_mn[a][0], s_mn[a][w]);
+        s_mx[a][0] = umax(s_mx[a][0], s_mx[a][w]);
+      }
+      s_md[0] = s_md[0] > s_md[w] ? s_md[0] : s_md[w];
+    }
+    for (int a = 0; a < 3; ++a) {
+      if (s_mn[a][0] != ~0ull) atomicMin(&g->acc_min[a], s_mn[a][0]);
+      if (s_mx[a][0] != 0ull) atomicMax(&g->acc_max[a], s_mx[a][0]);
+    }
+    if (s_md[0]) atomicMax(&g->acc_maxdiam, s_md[0]);
+  }
+}
+
+}  // namespace bdm
+
+// ---- launch wrappers (defined in the .cu files, called by the C ABI layer) ---------------------
+namespace bdm {
+
+struct AgentArrays {             // one SoA buffer of agents
+  double *x, *y, *z;
+  float* diam;
+  unsigned* id;
+  double* vol;                   // growth only (else nullptr)
+};
+
+struct MechBuffers {
+  AgentArrays pos;               // P0: current positions (x,y,z used) -- always the step's output
+  AgentArrays sorted;            // P1: positions gathered into canonical order (x,y,z used)
+  AgentArrays attr[2];           // diam/id/vol, ping-pong by step parity
+  unsigned *key, *rank, *perm, *skey, *nbr, *count, *start;
+  float4* p4;                    // mixed: box-relative offsets + radius, canonical order
+  unsigned long long* tiles[2];  // scan tile states (box scan, division scan)
+  unsigned* flag;                // growth: divide flags by id; also the division rank array
+  unsigned* drank;
+  unsigned max_tiles;
+};
+
+// grid.cu
+void launch_bounds(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                   int grid_blocks);
+void launch_finalize(cudaStream_t s, DevGrid* g, MechConsts c);
+void launch_key_hist(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
+void launch_scan(cudaStream_t s, unsigned* in, unsigned* out, const unsigned* n_items,
+                 unsigned long long* tiles, unsigned* tile_ctr, unsigned* err, int zero_input,
+                 int grid_blocks);
+void launch_scatter(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
+void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_attr,
+                   const AgentArrays& dst_attr, DevGrid* g, bool mixed, int grid_blocks);
+// mechanics.cu
+void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                  MechConsts c, bool mixed, int grid_blocks);
+void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                 double dv, double vdiv, int grid_blocks);
+void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                   double offset_frac, uint2 key, unsigned capacity, int grid_blocks);
+void launch_secrete(cudaStream_t s, const MechBuffers& b, DevGrid* g, float* grid,
+                    const int dims[3], const double origin[3], double h, float q,
+                    int grid_blocks);
+void launch_unsort(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                   double* ox, double* oy, double* oz, float* odiam, double* ovol,
+                   unsigned* onbr, unsigned* obox, int grid_blocks);
+void launch_step_done(cudaStream_t s, DevGrid* g);
+// diffusion.cu
+void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], float lambda,
+                 float mu_dt, double* partials, DevGrid* g);
+int ftcs_partials_needed(const int dims[3]);
+
+}  // namespace bdm

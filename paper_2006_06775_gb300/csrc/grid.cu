@@ -1,0 +1,216 @@
+// grid.cu -- uniform-grid rebuild of one step (BioDynaMo, arXiv 2006.06775, Sec. "Simulation
+// concepts", environment paragraph: equal boxes, agents assigned to boxes by centre, box size from
+// the largest agent).  GPU form: per-axis bounds -> grid finalize -> box id + histogram -> single-pass
+// prefix scan -> scatter -> canonicalising gather into (box, id) order (readings R5, R6).
+#include "common.cuh"
+#include "scan.cuh"
+
+namespace bdm {
+
+__global__ void __launch_bounds__(kBlock) k_bounds(const double* __restrict__ x,
+                                                   const double* __restrict__ y,
+                                                   const double* __restrict__ z,
+                                                   const float* __restrict__ diam, DevGrid* g) {
+  const unsigned n = g->n;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  unsigned md = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v[3] = {x[i], y[i], z[i]};
+    for (int a = 0; a < 3; ++a) {
+      unsigned long long e = enc_double(v[a]);
+      mn[a] = e < mn[a] ? e : mn[a];
+      mx[a] = e > mx[a] ? e : mx[a];
+    }
+    if (diam) {
+      unsigned d = __float_as_uint(diam[i]);
+      md = d > md ? d : md;
+    }
+  }
+  block_commit_bounds(mn, mx, md, g);
+}
+
+// Turn the accumulated bounds into this step's grid (reading R5), then reset the accumulators and
+// the scan tile counter for the next producer.  One thread.
+__global__ void k_finalize(DevGrid* g, MechConsts c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned n = g->n;
+  g->scan_ctr[0] = 0;
+  g->scan_ctr[1] = 0;
+  if (n == 0 || g->err) {
+    g->nbox = 0;
+    g->nbox1 = 1;
+  } else {
+    double R = c.interaction_radius > 0.0 ? c.interaction_radius
+                                          : (double)__uint_as_float(g->acc_maxdiam);
+    double L = c.box_length > 0.0 ? c.box_length : R;
+    bool ok = (R > 0.0) && (L >= R) && (L < 2048.0);
+    long long Lq = (long long)ceil(L * kQScale);
+    unsigned long long nbox = 1;
+    long long O[3];
+    int dims[3];
+    for (int a = 0; a < 3 && ok; ++a) {
+      double lo = dec_double(g->acc_min[a]), hi = dec_double(g->acc_max[a]);
+      ok = fabs(lo) < 1e9 && fabs(hi) < 1e9;  // quantise() needs |v| < 2^40
+      if (!ok) break;
+      long long Xlo = quantise(lo), Xhi = quantise(hi);
+      O[a] = Xlo;
+      long long d = (Xhi - Xlo) / Lq + 1;
+      ok = d > 0 && d < (1ll << 30);
+      dims[a] = (int)d;
+      nbox *= (unsigned long long)d;
+      if (nbox > 0xFFFFFFF0ull) ok = false;
+    }
+    if (!ok) {
+      atomicOr(&g->err, (unsigned)ERR_RADIUS);
+      g->nbox = 0;
+      g->nbox1 = 1;
+    } else if (nbox > c.box_capacity) {
+      atomicOr(&g->err, (unsigned)ERR_GRID_OVERFLOW);
+      g->nbox = 0;
+      g->nbox1 = 1;
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        g->O[a] = O[a];
+        g->dims[a] = dims[a];
+      }
+      g->Lq = Lq;
+      g->nbox = (unsigned)nbox;
+      g->nbox1 = (unsigned)nbox + 1;
+      g->R = R;
+      g->R2 = R * R;
+      g->Lf = (float)((double)Lq / kQScale);
+      g->R2f = (float)(R * R);
+      g->R2lo = g->R2f * (1.0f - 1.0f / 4096.0f);
+      g->R2hi = g->R2f * (1.0f + 1.0f / 4096.0f);
+      g->invLq = (float)(1.0 / (double)Lq);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    g->acc_min[a] = ~0ull;
+    g->acc_max[a] = 0ull;
+  }
+  g->acc_maxdiam = 0u;
+}
+
+// Box id of each agent (current order) and its arrival rank in the box histogram.
+__global__ void __launch_bounds__(kBlock) k_key_hist(const double* __restrict__ x,
+                                                     const double* __restrict__ y,
+                                                     const double* __restrict__ z,
+                                                     unsigned* __restrict__ key,
+                                                     unsigned* __restrict__ rank,
+                                                     unsigned* __restrict__ count, DevGrid* g) {
+  const unsigned n = g->nbox ? g->n : 0u;
+  const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const float inv = g->invLq;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int ix = box_div(quantise(x[i]) - O0, Lq, inv);
+    int iy = box_div(quantise(y[i]) - O1, Lq, inv);
+    int iz = box_div(quantise(z[i]) - O2, Lq, inv);
+    if (ix >= d0 || iy >= d1 || iz >= d2) {  // impossible by construction of the bounds
+      atomicOr(&g->err, (unsigned)ERR_BOUNDS);
+      ix = min(ix, d0 - 1); iy = min(iy, d1 - 1); iz = min(iz, d2 - 1);
+    }
+    unsigned k = (unsigned)ix + (unsigned)d0 * ((unsigned)iy + (unsigned)d1 * (unsigned)iz);
+    key[i] = k;
+    rank[i] = atomicAdd(&count[k], 1u);
+  }
+}
+
+// Exclusive scan of *n_items values (box histogram -> box starts, or division flags -> ranks).
+__global__ void __launch_bounds__(kBlock) k_scan(unsigned* __restrict__ in,
+                                                 unsigned* __restrict__ out,
+                                                 const unsigned* n_items,
+                                                 unsigned long long* tiles, unsigned* tile_ctr,
+                                                 unsigned* err, int zero_input) {
+  scan_tiles(in, out, *n_items, tiles, tile_ctr, err, zero_input);
+}
+
+// Counting-sort scatter: slot = box start + arrival rank.
+__global__ void __launch_bounds__(kBlock) k_scatter(const unsigned* __restrict__ key,
+                                                    const unsigned* __restrict__ rank,
+                                                    const unsigned* __restrict__ start,
+                                                    unsigned* __restrict__ perm, DevGrid* g) {
+  const unsigned n = g->nbox ? g->n : 0u;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    perm[start[key[i]] + rank[i]] = i;
+}
+
+// Canonicalise and gather: the arrival order inside a box is replaced by ascending id (R6), and the
+// agent payload moves into the canonical order.  The mixed-precision path also writes each agent's
+// FP32 offset from its box's lower corner (exact lattice difference, then one rounding) and radius.
+template <bool MIXED>
+__global__ void __launch_bounds__(kBlock) k_gather(
+    const unsigned* __restrict__ perm, const unsigned* __restrict__ key,
+    const unsigned* __restrict__ start, const double* __restrict__ sx,
+    const double* __restrict__ sy, const double* __restrict__ sz, AgentArrays src,
+    double* __restrict__ dx, double* __restrict__ dy, double* __restrict__ dz, AgentArrays dst,
+    unsigned* __restrict__ skey, float4* __restrict__ p4, DevGrid* g) {
+  const unsigned n = g->nbox ? g->n : 0u;
+  const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
+  const unsigned d0 = (unsigned)g->dims[0], d1 = (unsigned)g->dims[1];
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned s = perm[k];
+    const unsigned b = key[s];
+    const unsigned lo = start[b], hi = start[b + 1];
+    const unsigned myid = src.id[s];
+    unsigned d = lo;
+    if (hi - lo > 1) {
+      for (unsigned m = lo; m < hi; ++m)
+        if (m != k) d += src.id[perm[m]] < myid ? 1u : 0u;
+    }
+    const double x = sx[s], y = sy[s], z = sz[s];
+    const float di = src.diam[s];
+    dx[d] = x;
+    dy[d] = y;
+    dz[d] = z;
+    dst.diam[d] = di;
+    dst.id[d] = myid;
+    if (src.vol) dst.vol[d] = src.vol[s];
+    skey[d] = b;
+    if (MIXED) {
+      const unsigned ix = b % d0, t = b / d0;
+      const unsigned iy = t % d1, iz = t / d1;
+      const float ox = (float)(int)(quantise(x) - O0 - (long long)ix * Lq) * kQInv;
+      const float oy = (float)(int)(quantise(y) - O1 - (long long)iy * Lq) * kQInv;
+      const float oz = (float)(int)(quantise(z) - O2 - (long long)iz * Lq) * kQInv;
+      p4[d] = make_float4(ox, oy, oz, 0.5f * di);
+    }
+  }
+}
+
+// ---- launch wrappers -------------------------------------------------------------------------
+void launch_bounds(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                   int grid_blocks) {
+  k_bounds<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, attr.diam, g);
+}
+
+void launch_finalize(cudaStream_t s, DevGrid* g, MechConsts c) { k_finalize<<<1, 32, 0, s>>>(g, c); }
+
+void launch_key_hist(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
+  k_key_hist<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, b.key, b.rank, b.count, g);
+}
+
+void launch_scan(cudaStream_t s, unsigned* in, unsigned* out, const unsigned* n_items,
+                 unsigned long long* tiles, unsigned* tile_ctr, unsigned* err, int zero_input,
+                 int grid_blocks) {
+  k_scan<<<grid_blocks, kBlock, 0, s>>>(in, out, n_items, tiles, tile_ctr, err, zero_input);
+}
+
+void launch_scatter(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
+  k_scatter<<<grid_blocks, kBlock, 0, s>>>(b.key, b.rank, b.start, b.perm, g);
+}
+
+void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_attr,
+                   const AgentArrays& dst_attr, DevGrid* g, bool mixed, int grid_blocks) {
+  if (mixed)
+    k_gather<true><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
+                                                  b.pos.z, src_attr, b.sorted.x, b.sorted.y,
+                                                  b.sorted.z, dst_attr, b.skey, b.p4, g);
+  else
+    k_gather<false><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
+                                                   b.pos.z, src_attr, b.sorted.x, b.sorted.y,
+                                                   b.sorted.z, dst_attr, b.skey, b.p4, g);
+}
+
+}  // namespace bdm

@@ -1,0 +1,56 @@
+// sir.cuh -- device-side layout of the SIR model (single run and batched ensemble).
+#pragma once
+#include "common.cuh"
+
+namespace bdm {
+
+// Per-run constants (reading R10), in 2^-10 um lattice units.
+struct SirRun {
+  int L;                        // periodic cube side
+  int nb;                       // boxes per axis
+  int Lb;                       // box side = L / nb (>= r)
+  int s;                        // move bound per axis
+  unsigned long long span;      // 2 s + 1
+  long long r2;                 // infection radius squared
+  unsigned long long thr_inf;   // floor(p_inf * 2^32)
+  unsigned long long thr_rec;   // floor(p_rec * 2^32)
+  uint2 key;                    // Philox key (seed low word, run id)
+  unsigned agent_off, agent_n;  // agents of this run: [agent_off, agent_off + agent_n)
+  unsigned box_off;             // boxes of this run: [box_off, box_off + nb^3)
+};
+
+struct SirState {               // one ping-pong half, agents in id order
+  int *X, *Y, *Z;
+  unsigned char* st;
+};
+
+struct SirSingle {
+  SirState state[2];
+  unsigned *key, *rank, *perm, *count, *start, *ninf;
+  unsigned long long* tiles;
+  unsigned max_tiles;
+  SirRun run;
+};
+
+struct SirBatchDev {
+  SirState state[2];
+  unsigned *key, *rank, *perm, *count, *start, *ninf;
+  unsigned long long* tiles;
+  unsigned max_tiles;
+  const SirRun* run;            // [runs]
+  const unsigned* tile_run;     // work list: run of each 256-agent tile
+  const unsigned* tile_start;   // work list: first agent of each tile
+  unsigned ntiles, runs, total_agents, total_boxes;
+  unsigned* hist;               // [hist_len][runs][3] S/I/R after each step
+  unsigned hist_len;
+  unsigned* bar;                // grid barrier: [0] arrivals, [1] generation
+};
+
+void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int par, int grid_blocks,
+                     int scan_blocks);
+cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g, int blocks,
+                                unsigned spin_limit, bool cooperative);
+int sir_ensemble_blocks_per_sm();
+void launch_philox(cudaStream_t s, unsigned n, const uint4* ctr, const uint2* key, uint4* out);
+
+}  // namespace bdm

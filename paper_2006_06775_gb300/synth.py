@@ -63,15 +63,18 @@ def large_side(n: int, volume_fraction: float = VOLUME_FRACTION_LARGE) -> float:
     return (n * MEAN_SPHERE_VOLUME_8_12 / volume_fraction) ** (1.0 / 3.0)
 
 
-def large_mechanics(n: int = 100_000_000, seed: int = 2, grid_n: int = 512, with_grid=True):
-    """Large mechanics + diffusion population at 0.3 volume fraction (side 5662 um at 10^8)."""
+def large_mechanics(n: int = 100_000_000, seed: int = 2, grid_n: int = 512, with_grid=True,
+                    grid_side=None):
+    """Large mechanics + diffusion population at 0.3 volume fraction (side 5662 um at 10^8).
+    The substance grid spans grid_side (default: the population's cube)."""
     side = large_side(n)
     x, y, z, d = uniform_spheres(n, side, seed)
     params = dict(MECH_DEFAULTS, precision="mixed", seed=seed)
     inputs = dict(x=x, y=y, z=z, diameter=d, side=side)
     if with_grid and grid_n:
+        gs = side if grid_side is None else grid_side
         params.update(diffusion_enabled=1, grid_n=(grid_n, grid_n, grid_n),
-                      grid_origin=(0.0, 0.0, 0.0), voxel=side / grid_n, diffusion_coeff=0.4,
+                      grid_origin=(0.0, 0.0, 0.0), voxel=gs / grid_n, diffusion_coeff=0.4,
                       decay=0.01, dt_diffusion=1.0, secretion=0.0)
         inputs["grid"] = smooth_field(grid_n, seed)
     return params, inputs
