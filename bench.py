@@ -111,45 +111,54 @@ def make_workload(n, seed):
 # ------------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload
 # ------------------------------------------------------------------------------------------------
-def oracle_sample_rate(n_sample=2_000_000, steps=1, seed=2):
-    import oracle
-    frac = n_sample / 1e8
-    gn = max(8, int(round(512 * frac ** (1.0 / 3.0))))
-    params, inp = synth.large_mechanics(n=n_sample, seed=seed, grid_n=gn)
-    sim = oracle.OracleSim(params)
-    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
-    sim.set_grid(inp["grid"])
-    t0 = time.perf_counter()
-    sim.step(steps)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample * steps / dt, "unit": METRIC, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "%d step(s) of %d agents at the same density with a %d^3 grid (same voxel "
-                      "size), FP64, OpenMP over agents; %.1f s" % (steps, n_sample, gn, dt),
-            "seconds": dt}
+class OracleSample:
+    """The FP64 oracle on a bounded sample of the workload: n_sample agents at the same density in a
+    proportionally smaller cube, with a grid of the same voxel size."""
+
+    def __init__(self, n_sample, seed=2):
+        import oracle
+        self.oracle = oracle
+        self.n = n_sample
+        self.gn = max(8, int(round(512 * (n_sample / 1e8) ** (1.0 / 3.0))))
+        params, inp = synth.large_mechanics(n=n_sample, seed=seed, grid_n=self.gn)
+        self.sim = oracle.OracleSim(params)
+        self.sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+        self.sim.set_grid(inp["grid"])
+
+    def time_steps(self, steps):
+        t0 = time.perf_counter()
+        self.sim.step(steps)
+        return time.perf_counter() - t0
+
+    def describe(self, steps, secs):
+        return ("%d step(s) of %d agents at the workload's density with a %d^3 grid of the same "
+                "voxel size, FP64 oracle, OpenMP over agents; %.1f s" % (steps, self.n, self.gn, secs))
+
+
+def oracle_baseline(n_sample, steps=1):
+    s = OracleSample(n_sample)
+    secs = s.time_steps(steps)
+    return {"value": n_sample * steps / secs, "unit": METRIC, "cores": s.oracle.num_threads(),
+            "kind": "oracle", "sample": s.describe(steps, secs)}
 
 
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n_sample = args.cpu_sample
-    for _ in range(args.warmup):
-        oracle_sample_rate(n_sample, 1)
-    rates, secs = [], 0.0
-    for _ in range(args.steps):
-        r = oracle_sample_rate(n_sample, 1)
-        rates.append(r["value"])
-        secs += r["seconds"]
-    value = n_sample * args.steps / secs
+    s = OracleSample(args.cpu_sample)
+    s.time_steps(args.warmup)
+    secs = s.time_steps(args.steps)
+    value = s.n * args.steps / secs
+    cpu = {"value": value, "unit": METRIC, "cores": s.oracle.num_threads(), "kind": "oracle",
+           "sample": s.describe(args.steps, secs)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "agents": int(1e8), "grid": 512,
-                       "sample_agents": n_sample},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": r["cores"],
-                             "kind": "oracle", "sample": r["sample"]},
+                       "sample_agents": s.n},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -236,8 +245,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample_rate(args.cpu_sample, 1)
-        cpu.pop("seconds", None)
+        cpu = oracle_baseline(args.cpu_sample, 1)
 
     if rank == 0:
         line = {
@@ -309,7 +317,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--agents", type=int, default=100_000_000)
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=20_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

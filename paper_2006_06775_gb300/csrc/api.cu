@@ -400,7 +400,8 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
   const int stream_blocks = s->sms * 8;
   const size_t need = (C + kBlock - 1) / kBlock;
   s->blocks_stream = (int)std::max<size_t>(1, std::min<size_t>(need, stream_blocks));
-  s->blocks_force = (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)s->sms * 4));
+  s->blocks_force = s->mixed ? s->sms * force_mixed_blocks_per_sm()
+                             : (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)s->sms * 4));
   const size_t tiles = s->is_sir ? s->sb.max_tiles : s->mb.max_tiles;
   s->blocks_scan = (int)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)s->sms * 4));
   s->allocated = true;

@@ -98,6 +98,18 @@ __device__ __forceinline__ long long quantise(double v) {
   return (b >> 63) ? -(long long)q : (long long)q;
 }
 
+// Exact float -> double conversion with integer operations (normal numbers and zeros); other
+// encodings (subnormals, inf, NaN) take the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
+  if (e == 0u || e == 0xFFu) return (double)f;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 // floor(D / Lq) for 0 <= D < 2^62, 0 < Lq < 2^40: a float estimate corrected by exact products.
 __device__ __forceinline__ int box_div(long long D, long long Lq, float invLq) {
   float df = (float)(D >> 20) * 1048576.0f + (float)(D & 0xFFFFF);
@@ -137,10 +149,11 @@ __device__ __forceinline__ T warp_reduce(T v, Op op) {
 // Block-wide bounds commit: min/max of order-preserving centre encodings and the largest diameter
 // bits, one atomic per quantity per block.  Every thread of the block must call it.
 // ---------------------------------------------------------------------------------------------
+template <int NT = kBlock>
 __device__ __forceinline__ void block_commit_bounds(unsigned long long mn[3], unsigned long long mx[3],
                                     unsigned md, DevGrid* g) {
-  __shared__ unsigned long long s_mn[3][kBlock / 32], s_mx[3][kBlock / 32];
-  __shared__ unsigned s_md[kBlock / 32];
+  __shared__ unsigned long long s_mn[3][NT / 32], s_mx[3][NT / 32];
+  __shared__ unsigned s_md[NT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   auto umin = [](unsigned long long a, unsigned long long b) { return a < b ? a : b; };
   auto umax = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
@@ -158,7 +171,7 @@ __device__ __forceinline__ void block_commit_bounds(unsigned long long mn[3], un
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kBlock / 32; ++w) {
+    for (int w = 1; w < NT / 32; ++w) {
       for (int a = 0; a < 3; ++a) {
         s_mn[a][0] = umin(s_mn[a][0], s_mn[a][w]);
         s_mx[a][0] = umax(s_mx[a][0], s_mx[a][w]);
@@ -211,6 +224,7 @@ void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_
 // mechanics.cu
 void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                   MechConsts c, bool mixed, int grid_blocks);
+int force_mixed_blocks_per_sm();
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                  double dv, double vdiv, int grid_blocks);
 void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -83,6 +83,7 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
       g->R2lo = g->R2f * (1.0f - 1.0f / 4096.0f);
       g->R2hi = g->R2f * (1.0f + 1.0f / 4096.0f);
       g->invLq = (float)(1.0 / (double)Lq);
+
     }
   }
   for (int a = 0; a < 3; ++a) {

@@ -7,29 +7,21 @@
 namespace bdm {
 
 // ---------------------------------------------------------------------------------------------
-// Force + capped update, one thread per agent in canonical order.  Neighbours are read box by box
-// in ascending key -- for each (dz, dy) the up-to-three boxes along x are contiguous in the sorted
-// arrays -- which is exactly the oracle's (box, id) summation order.
-//
-// FP64 variant: every operation is an explicitly rounded FP64 intrinsic in the oracle's order (no
-// contraction), so positions can match the FP64 oracle bit for bit.
-// MIXED variant: pair geometry and forces in FP32 from box-relative offsets (all |values| < 2 L);
-// the neighbour predicate d^2 < R^2 is decided in FP32 outside a +-2^-12 relative band and by the
-// FP64 expression of the oracle inside it, so neighbour counts stay exact; the displacement is
-// added to the FP64 position.
-// The epilogue folds the new centres into the bounds of the next step's grid.
+// Force + capped update, FP64 check path: one thread per agent in canonical order.  Neighbours are
+// read box by box in ascending key -- for each (dz, dy) the up-to-three boxes along x are
+// contiguous in the sorted arrays -- which is exactly the oracle's (box, id) summation order.  Every
+// operation is an explicitly rounded FP64 intrinsic in the oracle's order (no contraction), so
+// positions can match the FP64 oracle bit for bit.  The epilogue folds the new centres into the
+// bounds of the next step's grid.
 // ---------------------------------------------------------------------------------------------
-template <bool MIXED>
-__global__ void __launch_bounds__(kBlock, MIXED ? 4 : 1) k_force(
+__global__ void __launch_bounds__(kBlock, 1) k_force_fp64(
     const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
-    const float* __restrict__ diam, const float4* __restrict__ p4,
-    const unsigned* __restrict__ skey, const unsigned* __restrict__ start,
-    double* __restrict__ ox, double* __restrict__ oy, double* __restrict__ oz,
-    unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
+    const float* __restrict__ diam, const unsigned* __restrict__ skey,
+    const unsigned* __restrict__ start, double* __restrict__ ox, double* __restrict__ oy,
+    double* __restrict__ oz, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
   const unsigned n = g->nbox ? g->n : 0u;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const double R2 = g->R2;
-  const float Lf = g->Lf, R2lo = g->R2lo, R2hi = g->R2hi;
   unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
   unsigned md = 0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -38,13 +30,9 @@ __global__ void __launch_bounds__(kBlock, MIXED ? 4 : 1) k_force(
     const unsigned t = b / (unsigned)d0;
     const int iy = (int)(t % (unsigned)d1), iz = (int)(t / (unsigned)d1);
     const double xi = sx[i], yi = sy[i], zi = sz[i];
+    const double ri = 0.5 * (double)diam[i];
     unsigned cnt = 0;
-    double Sx = 0.0, Sy = 0.0, Sz = 0.0;      // FP64 variant
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;       // MIXED variant
-    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-    double ri = 0.0;
-    if (MIXED) pi = p4[i];
-    else ri = 0.5 * (double)diam[i];
+    double Sx = 0.0, Sy = 0.0, Sz = 0.0;
     const int xlo = ix > 0 ? ix - 1 : 0, xhi = ix < d0 - 1 ? ix + 1 : d0 - 1;
     for (int dz = -1; dz <= 1; ++dz) {
       const int jz = iz + dz;
@@ -53,91 +41,36 @@ __global__ void __launch_bounds__(kBlock, MIXED ? 4 : 1) k_force(
         const int jy = iy + dy;
         if (jy < 0 || jy >= d1) continue;
         const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
-        unsigned s0 = start[row + xlo];
-        for (int bx = xlo; bx <= xhi; ++bx) {
-          const unsigned s1 = start[row + bx + 1];
-          if (MIXED) {
-            const float shx = (float)(bx - ix) * Lf, shy = (float)dy * Lf, shz = (float)dz * Lf;
-            for (unsigned j = s0; j < s1; ++j) {
-              if (j == i) continue;
-              const float4 q = p4[j];
-              const float ex = pi.x - (q.x + shx);
-              const float ey = pi.y - (q.y + shy);
-              const float ez = pi.z - (q.z + shz);
-              const float d2f = ex * ex + ey * ey + ez * ez;
-              if (d2f < R2lo) {
-                ++cnt;
-              } else if (d2f <= R2hi) {
-                const double ax = __dsub_rn(xi, sx[j]), ay = __dsub_rn(yi, sy[j]),
-                             az = __dsub_rn(zi, sz[j]);
-                const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)),
-                                            __dmul_rn(az, az));
-                cnt += e2 < R2 ? 1u : 0u;
-              }
-              const float rs = pi.w + q.w;
-              if (d2f < rs * rs && d2f > 0.f) {
-                const float rinv = rsqrtf(d2f);
-                const float dd = d2f * rinv;
-                const float delta = rs - dd;
-                if (delta > 0.f) {
-                  const float rd = __fdividef(pi.w * q.w, rs) * delta;  // rho * delta > 0
-                  const float F = c.kf * delta - c.gammaf * (rd * rsqrtf(rd));
-                  const float s = F * rinv;
-                  Fx += s * ex;
-                  Fy += s * ey;
-                  Fz += s * ez;
-                }
-              }
-            }
-          } else {
-            for (unsigned j = s0; j < s1; ++j) {
-              if (j == i) continue;
-              const double ax = __dsub_rn(xi, sx[j]), ay = __dsub_rn(yi, sy[j]),
-                           az = __dsub_rn(zi, sz[j]);
-              const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)),
-                                          __dmul_rn(az, az));
-              if (e2 < R2) ++cnt;
-              const double d = __dsqrt_rn(e2);
-              const double rj = 0.5 * (double)diam[j];
-              const double delta = __dsub_rn(__dadd_rn(ri, rj), d);
-              if (delta > 0.0 && d > 0.0) {
-                const double rho = __ddiv_rn(__dmul_rn(ri, rj), __dadd_rn(ri, rj));
-                const double F = __dsub_rn(__dmul_rn(c.k, delta),
-                                           __dmul_rn(c.gamma, __dsqrt_rn(__dmul_rn(rho, delta))));
-                const double s = __ddiv_rn(F, d);
-                Sx = __dadd_rn(Sx, __dmul_rn(s, ax));
-                Sy = __dadd_rn(Sy, __dmul_rn(s, ay));
-                Sz = __dadd_rn(Sz, __dmul_rn(s, az));
-              }
-            }
+        const unsigned s0 = start[row + xlo], s1 = start[row + xhi + 1];
+        for (unsigned j = s0; j < s1; ++j) {
+          if (j == i) continue;
+          const double ax = __dsub_rn(xi, sx[j]), ay = __dsub_rn(yi, sy[j]), az = __dsub_rn(zi, sz[j]);
+          const double e2 =
+              __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+          if (e2 < R2) ++cnt;
+          const double d = __dsqrt_rn(e2);
+          const double rj = 0.5 * (double)diam[j];
+          const double delta = __dsub_rn(__dadd_rn(ri, rj), d);
+          if (delta > 0.0 && d > 0.0) {
+            const double rho = __ddiv_rn(__dmul_rn(ri, rj), __dadd_rn(ri, rj));
+            const double F = __dsub_rn(__dmul_rn(c.k, delta),
+                                       __dmul_rn(c.gamma, __dsqrt_rn(__dmul_rn(rho, delta))));
+            const double s = __ddiv_rn(F, d);
+            Sx = __dadd_rn(Sx, __dmul_rn(s, ax));
+            Sy = __dadd_rn(Sy, __dmul_rn(s, ay));
+            Sz = __dadd_rn(Sz, __dmul_rn(s, az));
           }
-          s0 = s1;
         }
       }
     }
-    double nx, ny, nz;
-    if (MIXED) {
-      float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
-      const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
-      if (n2 > c.capf * c.capf) {
-        const float f = c.capf * rsqrtf(n2);
-        Dx *= f; Dy *= f; Dz *= f;
-      }
-      nx = __dadd_rn(xi, (double)Dx);
-      ny = __dadd_rn(yi, (double)Dy);
-      nz = __dadd_rn(zi, (double)Dz);
-    } else {
-      double Dx = __dmul_rn(c.dt, Sx), Dy = __dmul_rn(c.dt, Sy), Dz = __dmul_rn(c.dt, Sz);
-      double nrm = __dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy));
-      nrm = __dsqrt_rn(__dadd_rn(nrm, __dmul_rn(Dz, Dz)));
-      if (nrm > c.cap) {
-        const double f = __ddiv_rn(c.cap, nrm);
-        Dx = __dmul_rn(Dx, f); Dy = __dmul_rn(Dy, f); Dz = __dmul_rn(Dz, f);
-      }
-      nx = __dadd_rn(xi, Dx);
-      ny = __dadd_rn(yi, Dy);
-      nz = __dadd_rn(zi, Dz);
+    double Dx = __dmul_rn(c.dt, Sx), Dy = __dmul_rn(c.dt, Sy), Dz = __dmul_rn(c.dt, Sz);
+    double nrm = __dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy));
+    nrm = __dsqrt_rn(__dadd_rn(nrm, __dmul_rn(Dz, Dz)));
+    if (nrm > c.cap) {
+      const double f = __ddiv_rn(c.cap, nrm);
+      Dx = __dmul_rn(Dx, f); Dy = __dmul_rn(Dy, f); Dz = __dmul_rn(Dz, f);
     }
+    const double nx = __dadd_rn(xi, Dx), ny = __dadd_rn(yi, Dy), nz = __dadd_rn(zi, Dz);
     ox[i] = nx;
     oy[i] = ny;
     oz[i] = nz;
@@ -146,10 +79,187 @@ __global__ void __launch_bounds__(kBlock, MIXED ? 4 : 1) k_force(
     mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
     mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
     mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
-    const unsigned dbits = MIXED ? __float_as_uint(2.0f * pi.w) : __float_as_uint(diam[i]);
+    const unsigned dbits = __float_as_uint(diam[i]);
     md = dbits > md ? dbits : md;
   }
   block_commit_bounds(mn, mx, md, g);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Force + capped update, mixed precision.  One thread per agent in canonical order (grid-stride).
+// The nine row segments (dz, dy in {-1,0,1}) of its 27-box neighbourhood are contiguous runs of the
+// canonical order; each run is split by two box boundaries into its x-1, x, x+1 boxes (which give
+// the x shift of a candidate's box-relative offset).  Per candidate: FP32 d^2, the neighbour count,
+// a contact test; contacts are queued in four registers and flushed through the force law in order,
+// so the rare force evaluations (~9% of candidates) do not run masked in every iteration of the
+// candidate loop.  Contacts are summed in the canonical (box, id) order.  Loads go through L1:
+// consecutive agents share almost all of their neighbourhood.
+//
+// Neighbour predicate d^2 < R^2: FP32 outside a +-2^-12 relative band, the oracle's FP64 expression
+// inside it, so counts stay exact.  The agent meets itself once (d^2 = 0): counted, then removed.
+// The displacement is added to the FP64 centre (exact conversion, one FP64 add per axis).
+// ---------------------------------------------------------------------------------------------
+constexpr int kFT = 256;   // threads per CTA
+constexpr int kCL = 8;     // contact list length per thread
+
+__device__ __forceinline__ void contact_force(float& Fx, float& Fy, float& Fz, float ex, float ey,
+                                              float ez, float ri, float rj, float kf, float gf) {
+  const float d2 = ex * ex + ey * ey + ez * ez;
+  const float rs = ri + rj;
+  const float rinv = rsqrtf(d2);
+  const float delta = rs - d2 * rinv;
+  if (delta > 0.f) {
+    const float rd = __fdividef(ri * rj, rs) * delta;  // rho * delta > 0
+    const float F = kf * delta - gf * (rd * rsqrtf(rd));
+    const float sc = F * rinv;
+    Fx += sc * ex;
+    Fy += sc * ey;
+    Fz += sc * ez;
+  }
+}
+
+__device__ __forceinline__ unsigned fp64_within(unsigned i, unsigned j, const double* __restrict__ sx,
+                                                 const double* __restrict__ sy,
+                                                 const double* __restrict__ sz, double R2) {
+  const double ax = __dsub_rn(sx[i], sx[j]), ay = __dsub_rn(sy[i], sy[j]), az = __dsub_rn(sz[i], sz[j]);
+  const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+  return e2 < R2 ? 1u : 0u;
+}
+
+// Neighbours among the band candidates (FP32 d^2 within 2^-12 of R^2), decided by the oracle's FP64
+// expression.  Up to two were queued; more (vanishingly rare) are found again by a rescan.
+__device__ __forceinline__ unsigned exact_band_count(
+    unsigned i, unsigned nband, unsigned nb0, unsigned nb1, const double* __restrict__ sx,
+    const double* __restrict__ sy, const double* __restrict__ sz, const float4* __restrict__ p4,
+    const unsigned* __restrict__ start, int ix, int iy, int iz, int d0, int d1, int d2, float4 pi,
+    float Lf, float R2lo, float R2hi, double R2) {
+  if (nband <= 2) {
+    unsigned k = fp64_within(i, nb0, sx, sy, sz, R2);
+    if (nband == 2) k += fp64_within(i, nb1, sx, sy, sz, R2);
+    return k;
+  }
+  unsigned k = 0;
+  const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
+  for (int sg = 0; sg < 9; ++sg) {
+    const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
+    if (jz < 0 || jz >= d2 || jy < 0 || jy >= d1) continue;
+    const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
+    const unsigned a = start[row + xl], e = start[row + xh + 1];
+    const unsigned m1 = ix > 0 ? start[row + ix] : a, m2 = start[row + ix + 1];
+    const float py = pi.y - (float)(sg % 3 - 1) * Lf, pz = pi.z - (float)(sg / 3 - 1) * Lf;
+    for (unsigned j = a; j < e; ++j) {
+      const float4 q = p4[j];
+      const float px = pi.x - (j < m1 ? -Lf : (j < m2 ? 0.f : Lf));
+      const float ex = px - q.x, ey = py - q.y, ez = pz - q.z;
+      const float dd = ex * ex + ey * ey + ez * ez;
+      if (dd >= R2lo && dd <= R2hi) k += fp64_within(i, j, sx, sy, sz, R2);
+    }
+  }
+  return k;
+}
+
+__global__ void __launch_bounds__(kFT) k_force_mixed(
+    const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
+    const float4* __restrict__ p4, const unsigned* __restrict__ skey,
+    const unsigned* __restrict__ start, double* __restrict__ ox, double* __restrict__ oy,
+    double* __restrict__ oz, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
+  __shared__ unsigned s_cj[kCL][kFT];       // contact list: candidate index
+  __shared__ unsigned char s_cc[kCL][kFT];  // contact list: row segment * 3 + box x
+  const unsigned n = g->nbox ? g->n : 0u;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const double R2 = g->R2;
+  const float Lf = g->Lf, R2lo = g->R2lo, R2hi = g->R2hi;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  unsigned md = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned b = __ldg(skey + i);
+    const int ix = (int)(b % (unsigned)d0);
+    const unsigned q0 = b / (unsigned)d0;
+    const int iy = (int)(q0 % (unsigned)d1), iz = (int)(q0 / (unsigned)d1);
+    const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
+    const float4 pi = __ldg(p4 + i);
+    const double xi = sx[i], yi = sy[i], zi = sz[i];
+    const float pxm = pi.x + Lf, px0 = pi.x, pxp = pi.x - Lf;  // neighbour box at x-1, x, x+1
+    unsigned cnt = 0;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    int nc = 0;
+    // candidates with d^2 within 2^-12 of R^2 (decided in FP64 after the loop, so the FP64 code
+    // never runs predicated inside it)
+    unsigned nb0 = 0, nb1 = 0, nband = 0;
+    const int t = threadIdx.x;
+    auto flush = [&]() {  // force law over the listed contacts, in order
+      for (int k = 0; k < nc; ++k) {
+        const unsigned cj = s_cj[k][t], cc = s_cc[k][t];
+        const float4 q = __ldg(p4 + cj);
+        const int sgk = (int)(cc / 3u), bxk = (int)(cc % 3u);
+        const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q.x;
+        const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
+        const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
+        contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q.w, c.kf, c.gammaf);
+      }
+      nc = 0;
+    };
+#pragma unroll 1
+    for (int sg = 0; sg < 9; ++sg) {
+      const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
+      if (jz < 0 || jz >= d2 || jy < 0 || jy >= d1) continue;
+      const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
+      const unsigned a = __ldg(start + row + xl);
+      const unsigned m1 = ix > 0 ? __ldg(start + row + ix) : a;  // end of box x-1
+      const unsigned m2 = __ldg(start + row + ix + 1);           // end of box x
+      const unsigned e = __ldg(start + row + xh + 1);            // end of the run
+      const float py = pi.y - (float)(sg % 3 - 1) * Lf, pz = pi.z - (float)(sg / 3 - 1) * Lf;
+      for (unsigned j = a; j < e; ++j) {
+        const float4 q = __ldg(p4 + j);
+        const unsigned bx = j < m1 ? 0u : (j < m2 ? 1u : 2u);
+        const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
+        const float ey = py - q.y;
+        const float ez = pz - q.z;
+        const float dd = ex * ex + ey * ey + ez * ez;
+        cnt += dd < R2lo ? 1u : 0u;
+        if (dd >= R2lo && dd <= R2hi) {  // near R: queue for the FP64 decision after the loop
+          nb1 = nb0;
+          nb0 = j;
+          ++nband;
+        }
+        const float rs = pi.w + q.w;
+        s_cj[nc][t] = j;  // kept only if this is a contact
+        s_cc[nc][t] = (unsigned char)(sg * 3 + (int)bx);
+        nc += (dd < rs * rs && dd > 0.f) ? 1 : 0;
+        if (nc == kCL) flush();
+      }
+    }
+    flush();
+    if (nband) cnt += exact_band_count(i, nband, nb0, nb1, sx, sy, sz, p4, start, ix, iy, iz, d0, d1,
+                                       d2, pi, Lf, R2lo, R2hi, R2);
+    cnt -= 1u;  // the agent itself
+    float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
+    const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
+    if (n2 > c.capf * c.capf) {
+      const float f = c.capf * rsqrtf(n2);
+      Dx *= f; Dy *= f; Dz *= f;
+    }
+    const double nx = __dadd_rn(xi, f2d_exact(Dx));
+    const double ny = __dadd_rn(yi, f2d_exact(Dy));
+    const double nz = __dadd_rn(zi, f2d_exact(Dz));
+    ox[i] = nx;
+    oy[i] = ny;
+    oz[i] = nz;
+    nbr[i] = cnt;
+    const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
+    mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
+    mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
+    mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
+    const unsigned dbits = __float_as_uint(2.0f * pi.w);
+    md = dbits > md ? dbits : md;
+  }
+  block_commit_bounds<kFT>(mn, mx, md, g);
+}
+
+int force_mixed_blocks_per_sm() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, kFT, 0);
+  return nb > 0 ? nb : 1;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -290,13 +400,12 @@ __global__ void k_step_done(DevGrid* g) {
 void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                   MechConsts c, bool mixed, int grid_blocks) {
   if (mixed)
-    k_force<true><<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, attr.diam,
-                                                 b.p4, b.skey, b.start, b.pos.x, b.pos.y, b.pos.z,
-                                                 b.nbr, g, c);
+    k_force_mixed<<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.p4, b.skey,
+                                              b.start, b.pos.x, b.pos.y, b.pos.z, b.nbr, g, c);
   else
-    k_force<false><<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, attr.diam,
-                                                  b.p4, b.skey, b.start, b.pos.x, b.pos.y,
-                                                  b.pos.z, b.nbr, g, c);
+    k_force_fp64<<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, attr.diam,
+                                                b.skey, b.start, b.pos.x, b.pos.y, b.pos.z, b.nbr,
+                                                g, c);
 }
 
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -18,6 +18,7 @@ __device__ __forceinline__ void scan_tiles(unsigned* __restrict__ in, unsigned* 
   __shared__ unsigned s_tile;
   __shared__ unsigned s_warp[kBlock / 32];
   __shared__ unsigned s_exclusive;
+  __shared__ unsigned s_items[kScanTile + kScanTile / 32];  // striped -> blocked, padded
   const unsigned ntiles = (items + kScanTile - 1) / kScanTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   volatile unsigned long long* vt = tiles;
@@ -29,13 +30,21 @@ __device__ __forceinline__ void scan_tiles(unsigned* __restrict__ in, unsigned* 
       __syncthreads();  // everyone has read s_tile before a later call may overwrite it
       return;
     }
-    const unsigned base = tile * kScanTile + threadIdx.x * kScanItems;
+    const unsigned tbase = tile * kScanTile;
+    // coalesced striped load (item k * 256 + t), stored blocked per thread through shared memory
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned li = (unsigned)k * kBlock + threadIdx.x;
+      const unsigned idx = tbase + li;
+      s_items[li + (li >> 5)] = idx < items ? in[idx] : 0u;
+    }
+    __syncthreads();
     unsigned v[kScanItems];
     unsigned sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      unsigned idx = base + k;
-      v[k] = idx < items ? in[idx] : 0u;
+      const unsigned li = threadIdx.x * kScanItems + k;
+      v[k] = s_items[li + (li >> 5)];
       sum += v[k];
     }
     // block-wide exclusive scan of the per-thread sums
@@ -102,14 +111,21 @@ __device__ __forceinline__ void scan_tiles(unsigned* __restrict__ in, unsigned* 
     unsigned run = s_exclusive + thread_excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      unsigned idx = base + k;
-      if (idx < items) {
-        out[idx] = run;
-        if (zero_input) in[idx] = 0u;
-      }
+      const unsigned li = threadIdx.x * kScanItems + k;
+      s_items[li + (li >> 5)] = run;
       run += v[k];
     }
-    __syncthreads();  // s_tile / s_warp are reused by the next tile
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const unsigned li = (unsigned)k * kBlock + threadIdx.x;
+      const unsigned idx = tbase + li;
+      if (idx < items) {
+        out[idx] = s_items[li + (li >> 5)];
+        if (zero_input) in[idx] = 0u;
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next tile
   }
 }
 
