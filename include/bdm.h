@@ -188,6 +188,27 @@ const char* bdm_version(void);
  * device generator against independent implementations. */
 int bdm_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
+/* ---- Allocation-free diffusion step -------------------------------------------------------- */
+/* One FTCS step (same arithmetic as the diffusion co-step of bdm_step) for callers that cannot
+ * allocate device memory: applications that hand all device memory out of their own pool, code
+ * running while another framework captures a CUDA graph, or loops that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this is an interface
+ * variant of the library.
+ *   u, out   DEVICE grids of prod(grid_n) floats (x fastest), caller-owned, distinct.
+ *   grid_n   voxels per axis (host array); diffusion_coeff, dt_diffusion, voxel, decay as in
+ *            bdm_params (the step must be stable: D dt / h^2 <= 1/6).
+ *   mass     DEVICE double that receives the FP64 total of `out`, or NULL.
+ *   stream   cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * Allocates nothing: its scratch is a static device array of 65,536 doubles (512 KB per GPU that
+ * loads the library), so grids needing more than 65,536 blocks of 32 x 8 x 16 voxels are rejected
+ * with BDM_EINVAL (e.g. 512^3 uses 32,768).  The first call on a device looks up that array's
+ * address once; make it before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race on it, so order them (one stream, or events).  Returns BDM_EINVAL for bad
+ * arguments, BDM_ECUDA if the launch fails. */
+int bdm_diffusion_step_noalloc(const float* u, float* out, const int32_t grid_n[3],
+                               double diffusion_coeff, double dt_diffusion, double voxel,
+                               double decay, double* mass, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

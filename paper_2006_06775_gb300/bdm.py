@@ -94,6 +94,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.bdm_launch_count.restype = u64
     L.bdm_version.restype = ctypes.c_char_p
     L.bdm_philox.argtypes = [sz, vp, vp, vp]
+    L.bdm_diffusion_step_noalloc.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, vp, vp]
     _lib = L
     return L
 
@@ -257,6 +260,16 @@ def bdm_philox(ctr, key):
     out = np.zeros_like(ctr)
     _check(load().bdm_philox(ctr.shape[0], _ptr(ctr), _ptr(key), _ptr(out)))
     return out
+
+
+def bdm_diffusion_step_noalloc(u_ptr, out_ptr, grid_n, diffusion_coeff, dt_diffusion, voxel,
+                               decay, mass_ptr=None, stream=None):
+    """One FTCS step on caller-owned DEVICE buffers (integer device addresses); allocates nothing.
+    Returns the bdm status code."""
+    gn = (ctypes.c_int32 * 3)(*[int(v) for v in grid_n])
+    return load().bdm_diffusion_step_noalloc(u_ptr, out_ptr, gn, float(diffusion_coeff),
+                                             float(dt_diffusion), float(voxel), float(decay),
+                                             mass_ptr, stream)
 
 
 # ---- convenience wrapper ----------------------------------------------------------------------------

@@ -240,5 +240,7 @@ void launch_step_done(cudaStream_t s, DevGrid* g);
 void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], float lambda,
                  float mu_dt, double* partials, DevGrid* g);
 int ftcs_partials_needed(const int dims[3]);
+void launch_ftcs_mass_to(cudaStream_t s, const float* u, float* out, const int dims[3],
+                         float lambda, float mu_dt, double* partials, double* mass);
 
 }  // namespace bdm

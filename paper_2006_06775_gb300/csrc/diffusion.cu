@@ -71,6 +71,21 @@ __global__ void __launch_bounds__(1024) k_mass(const double* __restrict__ partia
   if (threadIdx.x == 0) g->mass = s[0];
 }
 
+// FP64 total of the block partials written to a caller-provided device slot (same order as k_mass).
+__global__ void __launch_bounds__(1024) k_mass_to(const double* __restrict__ partials, int count,
+                                                  double* __restrict__ out) {
+  __shared__ double s[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += 1024) acc += partials[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
 int ftcs_partials_needed(const int dims[3]) {
   return ((dims[0] + kFX - 1) / kFX) * ((dims[1] + kFY - 1) / kFY) * ((dims[2] + kFZ - 1) / kFZ);
 }
@@ -81,6 +96,14 @@ void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], 
   k_ftcs<<<grid, dim3(kFX, kFY), 0, s>>>(u, out, dims[0], dims[1], dims[2], lambda, mu_dt,
                                          partials);
   k_mass<<<1, 1024, 0, s>>>(partials, ftcs_partials_needed(dims), g);
+}
+
+void launch_ftcs_mass_to(cudaStream_t s, const float* u, float* out, const int dims[3],
+                         float lambda, float mu_dt, double* partials, double* mass) {
+  dim3 grid((dims[0] + kFX - 1) / kFX, (dims[1] + kFY - 1) / kFY, (dims[2] + kFZ - 1) / kFZ);
+  k_ftcs<<<grid, dim3(kFX, kFY), 0, s>>>(u, out, dims[0], dims[1], dims[2], lambda, mu_dt,
+                                         partials);
+  if (mass) k_mass_to<<<1, 1024, 0, s>>>(partials, ftcs_partials_needed(dims), mass);
 }
 
 }  // namespace bdm
