@@ -181,6 +181,47 @@ uint64_t bdm_launch_count(void);
 /* Library version string. */
 const char* bdm_version(void);
 
+/* ---- Batched SIR ensemble ------------------------------------------------------------------------ */
+/* Many SIR simulations (Sec. "Epidemiology use case": runs of the random-walk infection model with
+ * their own parameters) advanced together: every step is ONE persistent kernel launch covering all
+ * runs (a work list of (run, 256-agent tile) pairs; phases separated by a grid barrier whose waits
+ * are bounded), and n-step sequences are captured into a CUDA graph.  Each run computes exactly what
+ * a single-run handle would: the arithmetic is integer and per run. */
+typedef struct bdm_batch bdm_batch;
+typedef struct bdm_batch_options {
+  uint32_t struct_size;          /* = sizeof(bdm_batch_options)                                    */
+  uint32_t history_steps;        /* S/I/R counts kept per run (ring); 0 = 1024                     */
+  uint32_t spin_limit;           /* bounded-wait iterations of the grid barrier (~100 ns each);
+                                    0 = default (~0.4 s)                                          */
+  uint32_t barrier_extra;        /* test hook, 0 in normal use: arrivals the grid barrier waits for
+                                    beyond the launched grid, so that its bounded wait runs out and
+                                    the batch reports BDM_ETIMEOUT (no GPU fault)                 */
+  void* stream;                  /* cudaStream_t, NULL = a stream the batch creates               */
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* alloc_user;
+} bdm_batch_options;
+
+/* per_sim: `count` parameter blocks with kind = BDM_SIR (their seed/run_id key each run's Philox
+ * stream; sir_boxes 0 = about one agent per box).  opt may be NULL. */
+int bdm_batch_create(const bdm_params* per_sim, int count, const bdm_batch_options* opt,
+                     bdm_batch** out);
+/* Append agents (host arrays, um; sir_state NULL = susceptible) to run `sim`; only before the first
+ * step (the layout is fixed then). */
+int bdm_batch_add_agents(bdm_batch* b, int sim, size_t n, const double* x, const double* y,
+                         const double* z, const uint8_t* sir_state);
+/* Advance every run by n steps (asynchronous). */
+int bdm_batch_step(bdm_batch* b, int n);
+/* Wait for the batch's stream; BDM_ETIMEOUT if a grid-barrier wait ran out. */
+int bdm_batch_sync(bdm_batch* b);
+/* One run's state (agent-id order; box_id is run-local), like bdm_get_state. Synchronises. */
+int bdm_batch_get_state(bdm_batch* b, int sim, bdm_state* st);
+/* S/I/R counts after each of the last min(max_steps, history) steps, oldest first:
+ * out[step][run][3]; *steps receives the number of steps written.  Synchronises. */
+int bdm_batch_counts(bdm_batch* b, uint32_t* out, int max_steps, int* steps);
+void bdm_batch_destroy(bdm_batch* b);
+const char* bdm_batch_last_error(const bdm_batch* b);
+
 /* ---- Utility ----------------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind division axes and the SIR
  * behaviours, evaluated by the library's device code.  ctr: n x 4 words, key: n x 2 words, out:

@@ -63,6 +63,13 @@ class KernelTime(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("history_steps", ctypes.c_uint32),
+                ("spin_limit", ctypes.c_uint32), ("barrier_extra", ctypes.c_uint32),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -97,6 +104,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.bdm_diffusion_step_noalloc.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32),
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, vp, vp]
+    L.bdm_batch_create.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(BatchOptions),
+                                   ctypes.POINTER(vp)]
+    L.bdm_batch_add_agents.argtypes = [vp, i32, sz, vp, vp, vp, vp]
+    L.bdm_batch_step.argtypes = [vp, i32]
+    L.bdm_batch_sync.argtypes = [vp]
+    L.bdm_batch_get_state.argtypes = [vp, i32, ctypes.POINTER(State)]
+    L.bdm_batch_counts.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+    L.bdm_batch_destroy.argtypes = [vp]
+    L.bdm_batch_destroy.restype = None
+    L.bdm_batch_last_error.argtypes = [vp]
+    L.bdm_batch_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -270,6 +288,117 @@ def bdm_diffusion_step_noalloc(u_ptr, out_ptr, grid_n, diffusion_coeff, dt_diffu
     return load().bdm_diffusion_step_noalloc(u_ptr, out_ptr, gn, float(diffusion_coeff),
                                              float(dt_diffusion), float(voxel), float(decay),
                                              mass_ptr, stream)
+
+
+def _bcheck(rc, b):
+    if rc != BDM_OK:
+        raise BdmError(rc, load().bdm_batch_last_error(b).decode() if b else "")
+
+
+def bdm_batch_create(param_list, options=None):
+    arr = (Params * len(param_list))(*param_list)
+    b = ctypes.c_void_p()
+    rc = load().bdm_batch_create(arr, len(param_list), ctypes.byref(options) if options else None,
+                                 ctypes.byref(b))
+    if rc != BDM_OK:
+        msg = load().bdm_batch_last_error(b).decode() if b else ""
+        if b:
+            load().bdm_batch_destroy(b)
+        raise BdmError(rc, msg)
+    return b
+
+
+def bdm_batch_add_agents(b, sim, x, y, z, sir_state=None):
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    s = None if sir_state is None else np.ascontiguousarray(sir_state, np.uint8)
+    _bcheck(load().bdm_batch_add_agents(b, int(sim), len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(s)), b)
+
+
+def bdm_batch_step(b, n=1):
+    _bcheck(load().bdm_batch_step(b, int(n)), b)
+
+
+def bdm_batch_sync(b):
+    _bcheck(load().bdm_batch_sync(b), b)
+
+
+def bdm_batch_get_state(b, sim, fields=("x", "y", "z", "sir_state", "neighbour_count", "box_id")):
+    L = load()
+    st = State()
+    st.struct_size = ctypes.sizeof(State)
+    _bcheck(L.bdm_batch_get_state(b, int(sim), ctypes.byref(st)), b)
+    n = st.n
+    arrays = {f: np.empty(n, _DTYPES[f]) for f in fields}
+    st2 = State()
+    st2.struct_size = ctypes.sizeof(State)
+    for f, a in arrays.items():
+        setattr(st2, f, a.ctypes.data)
+    _bcheck(L.bdm_batch_get_state(b, int(sim), ctypes.byref(st2)), b)
+    arrays.update(n=int(st2.n), step=int(st2.step), sir_counts=np.array(st2.sir_counts[:], np.uint32))
+    return arrays
+
+
+def bdm_batch_counts(b, runs, max_steps):
+    out = np.zeros((max_steps, runs, 3), np.uint32)
+    got = ctypes.c_int(0)
+    _bcheck(load().bdm_batch_counts(b, _ptr(out), int(max_steps), ctypes.byref(got)), b)
+    return out[: got.value]
+
+
+def bdm_batch_destroy(b):
+    if b:
+        load().bdm_batch_destroy(b)
+
+
+class Batch:
+    """Batched SIR ensemble: one persistent launch per step for every run; memory from PyTorch."""
+
+    def __init__(self, param_dicts, history_steps=0, spin_limit=0, barrier_extra=0, stream=None,
+                 torch_memory=True):
+        import torch
+        self.runs = len(param_dicts)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        opt = BatchOptions()
+        opt.struct_size = ctypes.sizeof(BatchOptions)
+        opt.history_steps = int(history_steps)
+        opt.spin_limit = int(spin_limit)
+        opt.barrier_extra = int(barrier_extra)
+        opt.stream = self.stream.cuda_stream
+        self._allocator = None
+        if torch_memory:
+            self._allocator = TorchAllocator(self.stream)
+            opt.alloc = self._allocator.alloc_fn
+            opt.free = self._allocator.free_fn
+        self._opt = opt
+        self.h = bdm_batch_create([make_params(d) for d in param_dicts], opt)
+
+    def add_agents(self, sim, x, y, z, sir_state=None):
+        bdm_batch_add_agents(self.h, sim, x, y, z, sir_state)
+
+    def step(self, n=1):
+        bdm_batch_step(self.h, n)
+
+    def sync(self):
+        bdm_batch_sync(self.h)
+
+    def get_state(self, sim, **kw):
+        return bdm_batch_get_state(self.h, sim, **kw)
+
+    def counts(self, max_steps):
+        return bdm_batch_counts(self.h, self.runs, max_steps)
+
+    def close(self):
+        if self.h:
+            bdm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience wrapper ----------------------------------------------------------------------------

@@ -26,6 +26,9 @@ using namespace bdm;
 
 static std::atomic<unsigned long long> g_launches{0};
 
+// Kernel launches issued by other parts of the library (batched ensembles).
+void bdm_count_launches(unsigned long long k) { g_launches += k; }
+
 namespace {
 
 struct KernelStat {
@@ -248,19 +251,6 @@ unsigned long long threshold(double p) {
   return (unsigned long long)std::floor(p * 4294967296.0);
 }
 
-// SIR box count: the given one, else the largest divisor of the lattice side with box >= r and
-// about one agent per box.
-int sir_box_count(const bdm_params& p, size_t n) {
-  const long long L = std::llrint(p.sir_domain * 1024.0), r = std::llrint(p.sir_radius * 1024.0);
-  if (p.sir_boxes > 0) return p.sir_boxes;
-  long long limit = r > 0 ? L / r : L;
-  const long long target = std::max<long long>(1, (long long)std::cbrt((double)std::max<size_t>(n, 1)));
-  limit = std::min(limit, target);
-  for (long long nb = std::max<long long>(limit, 1); nb >= 1; --nb)
-    if (L % nb == 0) return (int)nb;
-  return 1;
-}
-
 // ---- allocation of the device state (first bdm_add_agents, or first step) --------------------
 int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const double* z,
              const float* d) {
@@ -282,7 +272,8 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
   }
   s->gh->nbox1 = 1;
   if (s->is_sir) {
-    const int nb = sir_box_count(p, n_first);
+    const int nb = sir_box_count(std::llrint(p.sir_domain * 1024.0), std::llrint(p.sir_radius * 1024.0),
+                                 p.sir_boxes, n_first);
     const long long Lu = std::llrint(p.sir_domain * 1024.0);
     const long long ru = std::llrint(p.sir_radius * 1024.0);
     if (Lu % nb != 0 || Lu / nb < ru)

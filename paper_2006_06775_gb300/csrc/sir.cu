@@ -240,7 +240,7 @@ void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int par, in
 }
 
 cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g, int blocks,
-                                unsigned spin_limit, bool cooperative) {
+                                unsigned barrier_extra, unsigned spin_limit, bool cooperative) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kBlock);
@@ -250,7 +250,8 @@ cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g
   attr[0].val.cooperative = cooperative ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_sir_ensemble, B, g, (unsigned)blocks, spin_limit);
+  return cudaLaunchKernelEx(&cfg, k_sir_ensemble, B, g, (unsigned)blocks + barrier_extra,
+                            spin_limit);
 }
 
 int sir_ensemble_blocks_per_sm() {

@@ -46,10 +46,23 @@ struct SirBatchDev {
   unsigned* bar;                // grid barrier: [0] arrivals, [1] generation
 };
 
+// Boxes per axis of a SIR grid: the given count, else the largest divisor of the lattice side L
+// (lattice units) that keeps the box side >= r and puts about one agent in a box.
+inline int sir_box_count(long long L, long long r, int given, size_t n) {
+  if (given > 0) return given;
+  long long limit = r > 0 ? L / r : L;
+  long long target = 1;
+  while ((target + 1) * (target + 1) * (target + 1) <= (long long)(n > 0 ? n : 1)) ++target;
+  if (target < limit) limit = target;
+  for (long long nb = limit > 1 ? limit : 1; nb >= 1; --nb)
+    if (L % nb == 0) return (int)nb;
+  return 1;
+}
+
 void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int par, int grid_blocks,
                      int scan_blocks);
 cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g, int blocks,
-                                unsigned spin_limit, bool cooperative);
+                                unsigned barrier_extra, unsigned spin_limit, bool cooperative);
 int sir_ensemble_blocks_per_sm();
 void launch_philox(cudaStream_t s, unsigned n, const uint4* ctr, const uint2* key, uint4* out);
 
