@@ -243,6 +243,13 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
 
+    sim.close()
+    ensemble = serving = None
+    if rank == 0 and not args.no_ensemble:
+        ensemble = bench_ensemble(args.ensemble_steps, args.ensemble_baseline_runs)
+    if rank == 0 and args.serve_requests > 0:
+        serving = bench_serving(args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(args.cpu_sample, 1)
@@ -267,12 +274,70 @@ def run_ours(args):
                               "frac": step_achieved / peak, "mechanics_ms_per_step": mech_ms},
             "kernels_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+            "ensemble": ensemble, "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_ensemble(steps, baseline_runs):
+    """Batched SIR ensemble (256 runs x 20,000 persons, one persistent launch per step) against the
+    same runs advanced one at a time with the single-run kernels (a sample of runs, scaled)."""
+    import torch
+    from paper_2006_06775_gb300 import bdm
+    ens = synth.sir_ensemble()
+    batch = bdm.Batch([p for p, _ in ens], history_steps=steps)
+    for k, (_, inp) in enumerate(ens):
+        batch.add_agents(k, inp["x"], inp["y"], inp["z"], inp["sir_state"])
+    batch.step(3)  # warm-up (builds the device layout, captures the graph)
+    batch.sync()
+    t0 = time.perf_counter()
+    batch.step(steps)
+    batch.sync()
+    t_batch = time.perf_counter() - t0
+    agents = sum(len(inp["x"]) for _, inp in ens)
+    # one at a time: the first `baseline_runs` runs, each alone, then scaled to all runs
+    t_single = 0.0
+    for k in range(baseline_runs):
+        p, inp = ens[k]
+        sim = bdm.Sim(p)
+        sim.add_agents(inp["x"], inp["y"], inp["z"], sir_state=inp["sir_state"])
+        sim.step(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(steps)
+        sim.get_state(fields=())
+        t_single += time.perf_counter() - t0
+        sim.close()
+    t_single *= len(ens) / baseline_runs
+    batch.close()
+    return {"workload": "256 SIR runs x 20,000 persons, 1000 um periodic cube",
+            "steps": steps, "agent_steps_per_s": agents * steps / t_batch,
+            "sims_per_s": len(ens) / t_batch, "ms_per_step": 1e3 * t_batch / steps,
+            "one_at_a_time_agent_steps_per_s": agents * steps / t_single,
+            "speedup_vs_one_at_a_time": t_single / t_batch,
+            "one_at_a_time_sample_runs": baseline_runs}
+
+
+def bench_serving(count):
+    """Served request stream (Poisson 200/s, sizes log-uniform 1e3..1e6, 50..500 steps, 70%
+    mechanics / 30% SIR, 150 GB budget) against the same trace one simulation at a time."""
+    from paper_2006_06775_gb300 import serve
+    reqs = synth.request_stream(count=count)
+    payloads = {r.rid: serve.payload(r) for r in reqs}
+    warm = [synth.Request(10 ** 6 + k, 0.0, kind, 2000, 10, 7 + k) for k, kind in
+            enumerate(("mechanics", "sir"))]
+    wp = {r.rid: serve.payload(r) for r in warm}
+    serve.run_one_at_a_time(serve.GpuExecutor(1), warm, lambda r: wp[r.rid])
+    served = serve.Server(serve.GpuExecutor(streams=8), budget_bytes=150e9, max_active=64,
+                          chunk=25).run(reqs, lambda r: payloads[r.rid])
+    alone = serve.run_one_at_a_time(serve.GpuExecutor(streams=1), reqs, lambda r: payloads[r.rid])
+    out = serve.summarize(served)
+    out["one_at_a_time"] = serve.summarize(alone)
+    out["trace"] = "first %d requests of the Poisson stream (seed 4)" % count
+    return out
 
 
 def run_e2e(sim, inp, n, steps, stream):
@@ -320,6 +385,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=1000)
+    ap.add_argument("--ensemble-baseline-runs", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
