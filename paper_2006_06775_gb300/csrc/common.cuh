@@ -110,9 +110,11 @@ __device__ __forceinline__ double f2d_exact(float f) {
                                           ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
-// floor(D / Lq) for 0 <= D < 2^62, 0 < Lq < 2^40: a float estimate corrected by exact products.
+// floor(D / Lq) for 0 <= D < 2^51, 0 < Lq < 2^40: a float estimate corrected by exact products.
+// The estimate converts two 32-bit halves (64-bit integer -> float conversions run on GB300's slow
+// conversion pipe).
 __device__ __forceinline__ int box_div(long long D, long long Lq, float invLq) {
-  float df = (float)(D >> 20) * 1048576.0f + (float)(D & 0xFFFFF);
+  float df = (float)(int)(D >> 20) * 1048576.0f + (float)(int)(D & 0xFFFFF);
   long long q = (long long)(int)(df * invLq);
   if (q < 0) q = 0;
   while (q > 0 && q * Lq > D) --q;
