@@ -67,7 +67,8 @@ typedef struct bdm_params {
   double box_length;             /* grid box L >= R; 0 = R                                         */
   /* Growth and division (reading R7). */
   int32_t growth_enabled;
-  int32_t reserved1;
+  int32_t force_variant;         /* mixed force kernel: 0 = one thread per agent, 1 = warp-shared
+                                    (agent, candidate) pairs; same results (tunable)              */
   double growth_volume;          /* volume added per step                                          */
   double division_volume;        /* divide when volume >= this                                     */
   double division_offset_frac;   /* mother/daughter offset = frac * daughter diameter             */

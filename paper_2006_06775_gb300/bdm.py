@@ -27,7 +27,7 @@ class Params(ctypes.Structure):
         ("dt", ctypes.c_double), ("repulsion", ctypes.c_double), ("attraction", ctypes.c_double),
         ("max_displacement", ctypes.c_double), ("interaction_radius", ctypes.c_double),
         ("box_length", ctypes.c_double),
-        ("growth_enabled", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("growth_enabled", ctypes.c_int32), ("force_variant", ctypes.c_int32),
         ("growth_volume", ctypes.c_double), ("division_volume", ctypes.c_double),
         ("division_offset_frac", ctypes.c_double),
         ("diffusion_enabled", ctypes.c_int32), ("grid_n", ctypes.c_int32 * 3),
@@ -149,7 +149,7 @@ def make_params(d: dict) -> Params:
                  "sir_step", "p_infect", "p_recover"):
         if name in d:
             setattr(p, name, float(d[name]))
-    for name in ("growth_enabled", "diffusion_enabled", "sir_boxes"):
+    for name in ("growth_enabled", "force_variant", "diffusion_enabled", "sir_boxes"):
         if name in d:
             setattr(p, name, int(d[name]))
     if "grid_n" in d:

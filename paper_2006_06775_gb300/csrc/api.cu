@@ -216,6 +216,8 @@ int check_params(bdm_sim* s, const bdm_params* p) {
       return fail(s, BDM_EINVAL, "repulsion/attraction must be finite and >= 0");
     if (!(p->interaction_radius >= 0.0) || !(p->box_length >= 0.0))
       return fail(s, BDM_EINVAL, "interaction_radius/box_length must be >= 0");
+    if (p->force_variant != 0 && p->force_variant != 1)
+      return fail(s, BDM_EINVAL, "force_variant must be 0 or 1");
     if (p->box_length > 0.0 && p->interaction_radius > 0.0 && p->box_length < p->interaction_radius)
       return fail(s, BDM_EINVAL, "box_length below interaction_radius");
     if (p->growth_enabled) {
@@ -373,6 +375,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     mc.box_length = p.box_length;
     mc.box_capacity = (unsigned)std::min<size_t>(boxcap, 0xFFFFFFF0ull);
     mc.capacity = (unsigned)C;
+    mc.force_variant = p.force_variant;
   }
   if (s->diffusion) {
     const size_t nv = (size_t)p.grid_n[0] * p.grid_n[1] * p.grid_n[2];
@@ -391,7 +394,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
   const int stream_blocks = s->sms * 8;
   const size_t need = (C + kBlock - 1) / kBlock;
   s->blocks_stream = (int)std::max<size_t>(1, std::min<size_t>(need, stream_blocks));
-  s->blocks_force = s->mixed ? s->sms * force_mixed_blocks_per_sm()
+  s->blocks_force = s->mixed ? s->sms * force_mixed_blocks_per_sm(s->mc.force_variant)
                              : (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)s->sms * 4));
   const size_t tiles = s->is_sir ? s->sb.max_tiles : s->mb.max_tiles;
   s->blocks_scan = (int)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)s->sms * 4));

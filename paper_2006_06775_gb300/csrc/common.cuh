@@ -61,6 +61,7 @@ struct MechConsts {               // per-simulation constants passed by value
   float dtf, kf, gammaf, capf;
   double interaction_radius, box_length;
   unsigned box_capacity, capacity;
+  int force_variant;              // 0: one thread per agent, 1: warp-shared pairs
 };
 
 // ---- exact helpers -------------------------------------------------------------------------
@@ -226,7 +227,7 @@ void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_
 // mechanics.cu
 void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                   MechConsts c, bool mixed, int grid_blocks);
-int force_mixed_blocks_per_sm();
+int force_mixed_blocks_per_sm(int variant);
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                  double dv, double vdiv, int grid_blocks);
 void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -256,9 +256,212 @@ __global__ void __launch_bounds__(kFT) k_force_mixed(
   block_commit_bounds<kFT>(mn, mx, md, g);
 }
 
-int force_mixed_blocks_per_sm() {
+// ---------------------------------------------------------------------------------------------
+// Force + capped update, mixed precision, warp-shared pairs (tunable alternative to one thread per
+// agent).  A warp owns 32 consecutive agents; for each of the nine rows the (agent, candidate)
+// pairs of all 32 agents are dealt out evenly over the lanes (owner table in shared memory), so
+// lanes stay busy regardless of how candidate counts vary between agents.  Counts are tallied with
+// shared-memory integer atomics; contacts are appended in pair order (ballot), which keeps each
+// agent's contacts in the canonical order, and each lane then evaluates its own contacts.  Same
+// arithmetic and outputs as k_force_mixed.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPW = kFT / 32;     // warps per CTA
+constexpr int kPairCap = 256;     // pairs per chunk of a row (owner table)
+constexpr int kConCap = 256;      // contact list per warp
+constexpr int kMyCap = 12;        // per-lane contact slots during a flush
+constexpr int kBandCap = 32;      // band list per warp
+
+__global__ void __launch_bounds__(kFT, 3) k_force_mixed_pairs(
+    const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
+    const float4* __restrict__ p4, const unsigned* __restrict__ skey,
+    const unsigned* __restrict__ start, double* __restrict__ ox, double* __restrict__ oy,
+    double* __restrict__ oz, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
+  __shared__ unsigned char s_own[kPW][kPairCap];
+  __shared__ uint4 s_run[kPW][32];
+  __shared__ float4 s_pi[kPW][32];
+  __shared__ unsigned s_cnt[kPW][32];
+  __shared__ unsigned s_cj[kPW][kConCap];
+  __shared__ unsigned short s_cinfo[kPW][kConCap];
+  __shared__ unsigned short s_my[kPW][kMyCap][32];
+  __shared__ unsigned s_bj[kPW][kBandCap];
+  __shared__ unsigned char s_bo[kPW][kBandCap];
+  __shared__ unsigned s_nb[kPW];
+  const unsigned n = g->nbox ? g->n : 0u;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const double R2 = g->R2;
+  const float Lf = g->Lf, R2lo = g->R2lo, R2hi = g->R2hi;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  unsigned md = 0;
+  const unsigned nwarps = gridDim.x * kPW;
+  for (unsigned base = (blockIdx.x * kPW + w) * 32u; base < n; base += nwarps * 32u) {
+    const unsigned i = base + lane;
+    const bool valid = i < n;
+    int ix = 0, iy = 0, iz = 0;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      const unsigned b = __ldg(skey + i);
+      ix = (int)(b % (unsigned)d0);
+      const unsigned q0 = b / (unsigned)d0;
+      iy = (int)(q0 % (unsigned)d1);
+      iz = (int)(q0 / (unsigned)d1);
+      pi = __ldg(p4 + i);
+    }
+    s_pi[w][lane] = pi;
+    s_cnt[w][lane] = 0u;
+    if (lane == 0) s_nb[w] = 0u;
+    unsigned nc = 0;  // contacts in the list (warp-uniform)
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
+    // Force law over the listed contacts: each lane collects its own entries (list order = the
+    // canonical order of its candidates) and evaluates them; the list is then empty.
+    auto flush = [&]() {
+      __syncwarp();
+      unsigned k = 0;
+      for (unsigned e = 0; e < nc; ++e) {
+        const unsigned info = s_cinfo[w][e];
+        if ((int)(info & 31u) == lane) {
+          if (k == (unsigned)kMyCap) {  // full: evaluate the slots, keep collecting
+            for (unsigned t = 0; t < k; ++t) {
+              const unsigned ee = s_my[w][t][lane];
+              const unsigned inf = s_cinfo[w][ee], cj = s_cj[w][ee];
+              const unsigned code = inf >> 5, sgk = code / 3u, bxk = code % 3u;
+              const float4 q = __ldg(p4 + cj);
+              const float ex = fmaf(-((float)bxk - 1.f), Lf, pi.x) - q.x;
+              const float ey = (pi.y - (float)((int)(sgk % 3u) - 1) * Lf) - q.y;
+              const float ez = (pi.z - (float)((int)(sgk / 3u) - 1) * Lf) - q.z;
+              contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q.w, c.kf, c.gammaf);
+            }
+            k = 0;
+          }
+          s_my[w][k++][lane] = (unsigned short)e;
+        }
+      }
+      for (unsigned t = 0; t < k; ++t) {
+        const unsigned ee = s_my[w][t][lane];
+        const unsigned inf = s_cinfo[w][ee], cj = s_cj[w][ee];
+        const unsigned code = inf >> 5, sgk = code / 3u, bxk = code % 3u;
+        const float4 q = __ldg(p4 + cj);
+        const float ex = fmaf(-((float)bxk - 1.f), Lf, pi.x) - q.x;
+        const float ey = (pi.y - (float)((int)(sgk % 3u) - 1) * Lf) - q.y;
+        const float ez = (pi.z - (float)((int)(sgk / 3u) - 1) * Lf) - q.z;
+        contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q.w, c.kf, c.gammaf);
+      }
+      nc = 0;
+      __syncwarp();
+    };
+    __syncwarp();
+#pragma unroll 1
+    for (int sg = 0; sg < 9; ++sg) {
+      const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
+      uint4 r = make_uint4(0u, 0u, 0u, 0u);  // a, end of box x-1, end of box x, end
+      if (valid && jz >= 0 && jz < d2 && jy >= 0 && jy < d1) {
+        const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
+        r.x = __ldg(start + row + xl);
+        r.y = ix > 0 ? __ldg(start + row + ix) : r.x;
+        r.z = __ldg(start + row + ix + 1);
+        r.w = __ldg(start + row + xh + 1);
+      }
+      const unsigned len = r.w - r.x;
+      unsigned P = len;  // inclusive scan over the warp
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xFFFFFFFFu, P, o);
+        if (lane >= o) P += t;
+      }
+      const unsigned T = __shfl_sync(0xFFFFFFFFu, P, 31);
+      P -= len;  // exclusive
+      s_run[w][lane] = make_uint4(r.x, r.y, r.z, P);
+      const float shy = (float)(sg % 3 - 1) * Lf, shz = (float)(sg / 3 - 1) * Lf;
+      for (unsigned c0 = 0; c0 < T; c0 += kPairCap) {
+        // owner table of pairs [c0, c0 + kPairCap)
+        const unsigned lo = P > c0 ? P : c0, hi = min(P + len, c0 + kPairCap);
+        for (unsigned p = lo; p < hi; ++p) s_own[w][p - c0] = (unsigned char)lane;
+        __syncwarp();
+        const unsigned cend = min(T, c0 + kPairCap);
+        for (unsigned p0 = c0; p0 < cend; p0 += 32) {
+          if (nc + 32u > (unsigned)kConCap) flush();
+          const unsigned p = p0 + lane;
+          const bool act = p < cend;
+          const unsigned o = act ? s_own[w][p - c0] : 0u;
+          const uint4 ro = s_run[w][o];
+          const float4 po = s_pi[w][o];
+          const unsigned j = ro.x + (p - ro.w);
+          bool con = false;
+          unsigned bx = 0;
+          if (act) {
+            const float4 q = __ldg(p4 + j);
+            bx = j < ro.y ? 0u : (j < ro.z ? 1u : 2u);
+            const float ex = fmaf(-((float)bx - 1.f), Lf, po.x) - q.x;
+            const float ey = (po.y - shy) - q.y;
+            const float ez = (po.z - shz) - q.z;
+            const float dd = ex * ex + ey * ey + ez * ez;
+            if (dd < R2lo) atomicAdd(&s_cnt[w][o], 1u);
+            else if (dd <= R2hi) {
+              const unsigned pos = atomicAdd(&s_nb[w], 1u);
+              if (pos < (unsigned)kBandCap) {
+                s_bj[w][pos] = j;
+                s_bo[w][pos] = (unsigned char)o;
+              }
+            }
+            const float rs = po.w + q.w;
+            con = dd < rs * rs && dd > 0.f;
+          }
+          const unsigned M = __ballot_sync(0xFFFFFFFFu, con);
+          if (con) {
+            const unsigned pos = nc + __popc(M & lt_mask);
+            s_cj[w][pos] = j;
+            s_cinfo[w][pos] = (unsigned short)(o | ((unsigned)(sg * 3 + (int)bx) << 5));
+          }
+          nc += __popc(M);
+        }
+        __syncwarp();
+      }
+    }
+    flush();
+    // neighbour count: own tally minus the agent itself, plus band candidates decided in FP64
+    unsigned cnt = s_cnt[w][lane] - 1u;
+    const unsigned nb = s_nb[w];
+    if (nb > (unsigned)kBandCap) {
+      // band list overflowed (very rare): every agent of the warp recounts its band exactly
+      if (valid) cnt += exact_band_count(i, 3u, 0u, 0u, sx, sy, sz, p4, start, ix, iy, iz, d0, d1, d2,
+                                         pi, Lf, R2lo, R2hi, R2);
+    } else {
+      for (unsigned e = 0; e < nb; ++e)
+        if (s_bo[w][e] == (unsigned char)lane) cnt += fp64_within(i, s_bj[w][e], sx, sy, sz, R2);
+    }
+    __syncwarp();
+    if (valid) {
+      const double xi = sx[i], yi = sy[i], zi = sz[i];
+      float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
+      const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
+      if (n2 > c.capf * c.capf) {
+        const float f = c.capf * rsqrtf(n2);
+        Dx *= f; Dy *= f; Dz *= f;
+      }
+      const double nx = __dadd_rn(xi, f2d_exact(Dx));
+      const double ny = __dadd_rn(yi, f2d_exact(Dy));
+      const double nz = __dadd_rn(zi, f2d_exact(Dz));
+      ox[i] = nx;
+      oy[i] = ny;
+      oz[i] = nz;
+      nbr[i] = cnt;
+      const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
+      mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
+      mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
+      mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
+      const unsigned dbits = __float_as_uint(2.0f * pi.w);
+      md = dbits > md ? dbits : md;
+    }
+  }
+  block_commit_bounds<kFT>(mn, mx, md, g);
+}
+
+int force_mixed_blocks_per_sm(int variant) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, kFT, 0);
+  if (variant == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed_pairs, kFT, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, kFT, 0);
   return nb > 0 ? nb : 1;
 }
 
@@ -399,7 +602,11 @@ __global__ void k_step_done(DevGrid* g) {
 // ---- launch wrappers -------------------------------------------------------------------------
 void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                   MechConsts c, bool mixed, int grid_blocks) {
-  if (mixed)
+  if (mixed && c.force_variant == 1)
+    k_force_mixed_pairs<<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.p4,
+                                                    b.skey, b.start, b.pos.x, b.pos.y, b.pos.z,
+                                                    b.nbr, g, c);
+  else if (mixed)
     k_force_mixed<<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.p4, b.skey,
                                               b.start, b.pos.x, b.pos.y, b.pos.z, b.nbr, g, c);
   else
