@@ -46,6 +46,7 @@ STEP_BYTES_PER_AGENT = lambda B: 4 * 32 + 8 * B  # rebuild + force + update, age
 FORCE_FLOP_PER_AGENT = lambda B: 9 * 27 * B + 13
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+TUNED_PATH = os.path.join(ROOT, "paper_2006_06775_gb300", "tuned.json")
 
 
 def measured_traffic(kernel, n):
@@ -217,6 +218,17 @@ def run_ours(args):
     bdm.load(build_if_missing=False)
     n = args.agents
     params, inp = make_workload(n, seed=2 + rank)
+    from paper_2006_06775_gb300 import tune
+    cache = tune.TuneCache(TUNED_PATH)
+    knobs = None
+    if args.tune:
+        cache.data.get(tune.gpu_name(), {}).pop(
+            tune.workload_signature(params, n, inp["side"] ** 3), None)
+        knobs = tune.tune_mechanics(params, inp, inp["side"] ** 3, cache=cache)
+    else:
+        knobs = cache.get(tune.workload_signature(params, n, inp["side"] ** 3), tune.gpu_name())
+    if knobs:
+        params = tune.mechanics_params(params, inp, knobs)
     stream = torch.cuda.Stream()
     sim = bdm.Sim(params, stream=stream)
     sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
@@ -306,6 +318,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "agents": n, "grid": 512, "precision": "mixed",
                        "boxes_per_agent": round(boxes_per_agent, 4),
+                       "tuned": ({"box_factor": knobs["box_factor"],
+                                  "force_variant": knobs["force_variant"]} if knobs else None),
                        "cache": "inputs larger than L2 (agent state ~12 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
@@ -425,6 +439,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", action="store_true",
+                    help="re-measure the tunable knobs on this workload and cache the choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=1000)

@@ -656,32 +656,21 @@ int bdm_add_agents(bdm_sim* s, size_t n, const double* x, const double* y, const
   }
   MechBuffers& b = s->mb;
   const AgentArrays& A = b.attr[s->attr_cur];
-  for (size_t i = 0; i < n; ++i)
-    if (!(diameter[i] > 0.0f) || !std::isfinite(x[i]) || !std::isfinite(y[i]) || !std::isfinite(z[i]) ||
-        std::fabs(x[i]) >= 1e9 || std::fabs(y[i]) >= 1e9 || std::fabs(z[i]) >= 1e9)
-      return fail(s, BDM_EINVAL, "agent %zu: diameter must be > 0 and |position| < 1e9", i);
   CK(cudaMemcpyAsync(b.pos.x + n0, x, n * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b.pos.y + n0, y, n * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b.pos.z + n0, z, n * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(A.diam + n0, diameter, n * sizeof(float), cudaMemcpyHostToDevice, st));
-  std::vector<unsigned> ids(n);
-  for (size_t i = 0; i < n; ++i) ids[i] = (unsigned)(n0 + i);
-  CK(cudaMemcpyAsync(A.id + n0, ids.data(), n * sizeof(unsigned), cudaMemcpyHostToDevice, st));
-  std::vector<double> vols;
-  if (s->growth) {
-    if (volume) {
-      CK(cudaMemcpyAsync(A.vol + n0, volume, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    } else {
-      vols.resize(n);
-      for (size_t i = 0; i < n; ++i) {
-        const double d = (double)diameter[i];
-        vols[i] = (0.5235987755982988 * d) * d * d;  // (pi/6) d^3
-      }
-      CK(cudaMemcpyAsync(A.vol + n0, vols.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-    }
-  }
-  CK(cudaMemsetAsync(b.nbr + n0, 0, n * sizeof(unsigned), st));
-  CK(cudaMemsetAsync(b.skey + n0, 0, n * sizeof(unsigned), st));
+  if (s->growth && volume)
+    CK(cudaMemcpyAsync(A.vol + n0, volume, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  // validation, ids, derived volumes and cleared outputs on the device; the count is committed only
+  // once the upload has been checked
+  CK(cudaMemsetAsync(&s->g->bad_input, 0xFF, sizeof(unsigned), st));
+  RUN("prepare", 1, launch_prepare_agents(st, (unsigned)n0, (unsigned)n, b.pos.x, b.pos.y, b.pos.z, A.diam, A.id,
+                                          A.vol, s->growth && !volume, b.nbr, b.skey, s->g, s->blocks_stream));
+  CK(cudaMemcpyAsync(&s->gh->bad_input, &s->g->bad_input, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (s->gh->bad_input != 0xFFFFFFFFu)
+    return fail(s, BDM_EINVAL, "agent %u: diameter must be > 0 and |position| < 1e9", s->gh->bad_input);
   s->n_stage = (unsigned)(n0 + n);
   CK(cudaMemcpyAsync(&s->g->n, &s->n_stage, sizeof(unsigned), cudaMemcpyHostToDevice, st));
   s->n_host = n0 + n;
@@ -698,11 +687,8 @@ int bdm_set_grid(bdm_sim* s, const float* values) {
   if (!values) return fail(s, BDM_EINVAL, "values is NULL");
   if ((rc = ensure_allocated(s))) return rc;
   const size_t nv = (size_t)s->gdims[0] * s->gdims[1] * s->gdims[2];
-  double mass = 0.0;
-  for (size_t i = 0; i < nv; ++i) mass += (double)values[i];
   CK(cudaMemcpyAsync(s->grid[s->grid_cur], values, nv * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-  s->gh->mass = mass;
-  CK(cudaMemcpyAsync(&s->g->mass, &s->gh->mass, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  RUN("grid_mass", 2, launch_grid_mass(s->stream, s->grid[s->grid_cur], s->gdims, s->partials, s->g));
   CK(cudaStreamSynchronize(s->stream));
   return BDM_OK;
 }

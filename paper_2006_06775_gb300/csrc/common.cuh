@@ -53,6 +53,7 @@ struct DevGrid {
   unsigned err;                   // ErrBit flags
   unsigned sir_counts[3];         // S, I, R after the last SIR step
   unsigned long long step;        // steps completed (Philox counters)
+  unsigned bad_input;             // first rejected agent of the last upload (~0u: none)
   double mass;                    // FP64 substance total after the last diffusion step
 };
 
@@ -239,10 +240,15 @@ void launch_unsort(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr
                    double* ox, double* oy, double* oz, float* odiam, double* ovol,
                    unsigned* onbr, unsigned* obox, int grid_blocks);
 void launch_step_done(cudaStream_t s, DevGrid* g);
+void launch_prepare_agents(cudaStream_t s, unsigned n0, unsigned n, const double* x, const double* y,
+                           const double* z, const float* diam, unsigned* id, double* vol,
+                           bool derive_volume, unsigned* nbr, unsigned* skey, DevGrid* g,
+                           int grid_blocks);
 // diffusion.cu
 void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], float lambda,
                  float mu_dt, double* partials, DevGrid* g);
 int ftcs_partials_needed(const int dims[3]);
+void launch_grid_mass(cudaStream_t s, const float* u, const int dims[3], double* partials, DevGrid* g);
 void launch_ftcs_mass_to(cudaStream_t s, const float* u, float* out, const int dims[3],
                          float lambda, float mu_dt, double* partials, double* mass);
 

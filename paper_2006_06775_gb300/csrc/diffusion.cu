@@ -86,6 +86,30 @@ __global__ void __launch_bounds__(1024) k_mass_to(const double* __restrict__ par
   if (threadIdx.x == 0) *out = s[0];
 }
 
+// FP64 total of a grid with the FTCS block layout: FP32 sums of 16 voxels per thread, FP64 per block.
+__global__ void __launch_bounds__(kFX* kFY) k_grid_partials(const float* __restrict__ u, int nx,
+                                                            int ny, int nz,
+                                                            double* __restrict__ partials) {
+  const int x = blockIdx.x * kFX + threadIdx.x;
+  const int y = blockIdx.y * kFY + threadIdx.y;
+  const int z0 = blockIdx.z * kFZ;
+  const int z1 = min(z0 + kFZ, nz);
+  const size_t plane = (size_t)nx * (size_t)ny;
+  float part = 0.f;
+  if (x < nx && y < ny)
+    for (int z = z0; z < z1; ++z) part += u[(size_t)x + (size_t)nx * (size_t)y + plane * (size_t)z];
+  __shared__ double s_part[kFX * kFY / 32];
+  double dp = warp_reduce((double)part, [](double a, double b) { return a + b; });
+  const int t = threadIdx.x + kFX * threadIdx.y;
+  if ((t & 31) == 0) s_part[t >> 5] = dp;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kFX * kFY / 32; ++w) s += s_part[w];
+    partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+  }
+}
+
 int ftcs_partials_needed(const int dims[3]) {
   return ((dims[0] + kFX - 1) / kFX) * ((dims[1] + kFY - 1) / kFY) * ((dims[2] + kFZ - 1) / kFZ);
 }
@@ -95,6 +119,12 @@ void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], 
   dim3 grid((dims[0] + kFX - 1) / kFX, (dims[1] + kFY - 1) / kFY, (dims[2] + kFZ - 1) / kFZ);
   k_ftcs<<<grid, dim3(kFX, kFY), 0, s>>>(u, out, dims[0], dims[1], dims[2], lambda, mu_dt,
                                          partials);
+  k_mass<<<1, 1024, 0, s>>>(partials, ftcs_partials_needed(dims), g);
+}
+
+void launch_grid_mass(cudaStream_t s, const float* u, const int dims[3], double* partials, DevGrid* g) {
+  dim3 grid((dims[0] + kFX - 1) / kFX, (dims[1] + kFY - 1) / kFY, (dims[2] + kFZ - 1) / kFZ);
+  k_grid_partials<<<grid, dim3(kFX, kFY), 0, s>>>(u, dims[0], dims[1], dims[2], partials);
   k_mass<<<1, 1024, 0, s>>>(partials, ftcs_partials_needed(dims), g);
 }
 

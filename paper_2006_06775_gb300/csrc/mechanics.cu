@@ -595,6 +595,30 @@ __global__ void __launch_bounds__(kBlock) k_unsort(
   }
 }
 
+// Upload of new agents (slots n0 .. n0 + n - 1): validate, assign dense ids, derive volumes
+// ((pi/6) d^3 in the order ((pi/6 * d) * d) * d) and clear the per-agent outputs.  The first
+// rejected agent (diameter <= 0, non-finite centre, |centre| >= 1e9 um) is recorded in bad_input.
+__global__ void __launch_bounds__(kBlock) k_prepare_agents(
+    unsigned n0, unsigned n, const double* __restrict__ x, const double* __restrict__ y,
+    const double* __restrict__ z, const float* __restrict__ diam, unsigned* __restrict__ id,
+    double* __restrict__ vol, int derive_volume, unsigned* __restrict__ nbr,
+    unsigned* __restrict__ skey, DevGrid* g) {
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned i = n0 + k;
+    const double px = x[i], py = y[i], pz = z[i];
+    const float d = diam[i];
+    const bool ok = d > 0.0f && fabs(px) < 1e9 && fabs(py) < 1e9 && fabs(pz) < 1e9;  // NaN fails
+    if (!ok) atomicMin(&g->bad_input, k);
+    id[i] = i;
+    if (derive_volume) {
+      const double dd = (double)d;
+      vol[i] = __dmul_rn(__dmul_rn(__dmul_rn(0.5235987755982988, dd), dd), dd);
+    }
+    nbr[i] = 0u;
+    skey[i] = 0u;
+  }
+}
+
 __global__ void k_step_done(DevGrid* g) {
   if (threadIdx.x == 0 && blockIdx.x == 0) g->step += 1ull;
 }
@@ -641,5 +665,13 @@ void launch_unsort(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr
 }
 
 void launch_step_done(cudaStream_t s, DevGrid* g) { k_step_done<<<1, 32, 0, s>>>(g); }
+
+void launch_prepare_agents(cudaStream_t s, unsigned n0, unsigned n, const double* x, const double* y,
+                           const double* z, const float* diam, unsigned* id, double* vol,
+                           bool derive_volume, unsigned* nbr, unsigned* skey, DevGrid* g,
+                           int grid_blocks) {
+  k_prepare_agents<<<grid_blocks, kBlock, 0, s>>>(n0, n, x, y, z, diam, id, vol,
+                                                  derive_volume ? 1 : 0, nbr, skey, g);
+}
 
 }  // namespace bdm

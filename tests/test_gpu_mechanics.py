@@ -308,3 +308,24 @@ def test_resume_is_bit_exact():
     res = c.get_state()
     for f in ("x", "y", "z", "diameter", "volume", "neighbour_count", "box_id"):
         assert np.array_equal(full[f], res[f]), f
+
+
+def test_invalid_agents_are_rejected_and_handle_stays_usable():
+    params = dict(synth.MECH_DEFAULTS, precision="fp64", capacity=64)
+    sim = bdm.Sim(params)
+    bad = ragged(10, 50.0, 3)
+    bad["diameter"][4] = 0.0
+    with pytest.raises(bdm.BdmError) as e:
+        sim.add_agents(bad["x"], bad["y"], bad["z"], bad["diameter"])
+    assert e.value.code == bdm.BDM_EINVAL and "agent 4" in str(e.value)
+    nan = ragged(10, 50.0, 4)
+    nan["y"][7] = float("nan")
+    with pytest.raises(bdm.BdmError):
+        sim.add_agents(nan["x"], nan["y"], nan["z"], nan["diameter"])
+    good = ragged(20, 50.0, 5)
+    ref = oracle.OracleSim(params)
+    for s in (sim, ref):
+        s.add_agents(good["x"], good["y"], good["z"], good["diameter"])
+    sim.step(2)
+    ref.step(2)
+    assert_step_equal(sim.get_state(), ref.get_state())
