@@ -342,7 +342,11 @@ def bench_ensemble(steps, baseline_runs):
     same runs advanced one at a time with the single-run kernels (a sample of runs, scaled)."""
     import torch
     from paper_2006_06775_gb300 import bdm
+    from paper_2006_06775_gb300 import tune
     ens = synth.sir_ensemble()
+    choice = tune.tune_sir_batch([p for p, _ in ens], [inp for _, inp in ens],
+                                 cache=tune.TuneCache(TUNED_PATH))
+    ens = [(dict(p, sir_boxes=choice["sir_boxes"]), inp) for p, inp in ens]
     batch = bdm.Batch([p for p, _ in ens], history_steps=steps)
     for k, (_, inp) in enumerate(ens):
         batch.add_agents(k, inp["x"], inp["y"], inp["z"], inp["sir_state"])
@@ -369,7 +373,7 @@ def bench_ensemble(steps, baseline_runs):
     t_single *= len(ens) / baseline_runs
     batch.close()
     return {"workload": "256 SIR runs x 20,000 persons, 1000 um periodic cube",
-            "steps": steps, "agent_steps_per_s": agents * steps / t_batch,
+            "steps": steps, "sir_boxes_per_axis": choice["sir_boxes"], "agent_steps_per_s": agents * steps / t_batch,
             "sims_per_s": len(ens) / t_batch, "ms_per_step": 1e3 * t_batch / steps,
             "one_at_a_time_agent_steps_per_s": agents * steps / t_single,
             "speedup_vs_one_at_a_time": t_single / t_batch,

@@ -5,9 +5,12 @@
 // Reading R10: synchronous integer step on a 2^-10 um lattice, periodic cube, Philox4x32-10 keyed
 // by (seed, run) with counters (id, step, stream, 0).
 //
-// Agents stay in id order; the uniform grid is an index (box -> agent ids) rebuilt every step by
-// counting sort.  One run uses four kernels per step; a batch of runs uses ONE persistent kernel per
-// step whose phases are separated by a bounded grid barrier.
+// Agents stay in id order.  Every agent's box id is computed each step, and the uniform grid index
+// (box -> agent ids, rebuilt by counting sort) holds the INFECTED agents only: the infection rule and
+// the infected-neighbour count only ever look at infected agents, so searching the 27 boxes of this
+// index gives exactly the counts of a full index at a fraction of the candidates.  One run uses four
+// kernels per step; a batch of runs uses ONE persistent kernel per step whose phases are separated
+// by a bounded grid barrier.
 #include "common.cuh"
 #include "scan.cuh"
 #include "sir.cuh"
@@ -56,8 +59,8 @@ __device__ __forceinline__ unsigned char sir_update(unsigned a, const SirRun& r,
                            (unsigned)r.nb * ((unsigned)cy[qy] + (unsigned)r.nb * (unsigned)cz[qz]);
         const unsigned e = start[b + 1];
         for (unsigned m = start[b]; m < e; ++m) {
-          const unsigned j = perm[m];
-          if (j == a || cur.st[j] != 1) continue;
+          const unsigned j = perm[m];  // an infected agent
+          if (j == a) continue;
           const long long dx = min_image((long long)Xi - cur.X[j], L);
           const long long dy = min_image((long long)Yi - cur.Y[j], L);
           const long long dz = min_image((long long)Zi - cur.Z[j], L);
@@ -116,16 +119,17 @@ __global__ void __launch_bounds__(kBlock) k_sir_keyhist(SirState cur, unsigned* 
   for (unsigned a = tid; a < n; a += gridDim.x * blockDim.x) {
     const unsigned b = sir_box(cur.X[a], cur.Y[a], cur.Z[a], r);
     key[a] = b;
-    rank[a] = atomicAdd(&count[b], 1u);
+    if (cur.st[a] == 1) rank[a] = atomicAdd(&count[b], 1u);
   }
 }
 
 __global__ void __launch_bounds__(kBlock) k_sir_scatter(const unsigned* __restrict__ key,
                                                         const unsigned* __restrict__ rank,
+                                                        const unsigned char* __restrict__ st,
                                                         const unsigned* __restrict__ start,
                                                         unsigned* __restrict__ perm, unsigned n) {
   for (unsigned a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x)
-    perm[start[key[a]] + rank[a]] = a;
+    if (st[a] == 1) perm[start[key[a]] + rank[a]] = a;
 }
 
 __global__ void __launch_bounds__(kBlock) k_sir_update(SirState cur, SirState nxt,
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_sir_ensemble(SirBatchDev B, DevGrid*
     if (a < r.agent_off + r.agent_n) {
       const unsigned b = r.box_off + sir_box(cur.X[a], cur.Y[a], cur.Z[a], r);
       B.key[a] = b;
-      B.rank[a] = atomicAdd(&B.count[b], 1u);
+      if (cur.st[a] == 1) B.rank[a] = atomicAdd(&B.count[b], 1u);
     }
   }
   grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kBlock) k_sir_ensemble(SirBatchDev B, DevGrid*
   grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
   // P3: scatter agent indices into box order
   for (unsigned a = tid; a < B.total_agents; a += nthreads)
-    B.perm[B.start[B.key[a]] + B.rank[a]] = a;
+    if (cur.st[a] == 1) B.perm[B.start[B.key[a]] + B.rank[a]] = a;
   grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
   // P4: infection, recovery, move; per-run S/I/R counts of this step
   for (unsigned t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
@@ -234,7 +238,7 @@ void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int par, in
   k_sir_keyhist<<<grid_blocks, kBlock, 0, s>>>(cur, S.key, S.rank, S.count, S.run, g);
   cudaMemsetAsync(S.tiles, 0, sizeof(unsigned long long) * S.max_tiles, s);
   launch_scan(s, S.count, S.start, &g->nbox1, S.tiles, &g->scan_ctr[0], &g->err, 1, scan_blocks);
-  k_sir_scatter<<<grid_blocks, kBlock, 0, s>>>(S.key, S.rank, S.start, S.perm, S.run.agent_n);
+  k_sir_scatter<<<grid_blocks, kBlock, 0, s>>>(S.key, S.rank, cur.st, S.start, S.perm, S.run.agent_n);
   k_sir_update<<<grid_blocks, kBlock, 0, s>>>(cur, nxt, S.start, S.perm, S.ninf, S.run, g);
   launch_step_done(s, g);
 }
