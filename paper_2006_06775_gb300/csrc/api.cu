@@ -85,7 +85,7 @@ struct Profiler {
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   unsigned long long kernels = 0;
-  int attr_cur = 0, grid_cur = 0, sir_par = 0;
+  int attr_cur = 0, grid_cur = 0;
   bool bounds_fresh = false;
 };
 
@@ -117,11 +117,10 @@ struct bdm_sim {
   int gdims[3] = {0, 0, 0};
   float lam = 0.f, mu_dt = 0.f;
   SirSingle sb{};
-  int sir_par = 0;
   std::vector<void*> allocs;
-  // n-step graphs keyed by (steps, diffusion only, attr parity, grid parity, SIR parity, bounds
-  // fresh, SIR agent count): each key fixes every pointer and launch size the capture saw
-  std::map<std::tuple<int, int, int, int, int, int, size_t>, GraphEntry> graphs;
+  // n-step graphs keyed by (steps, diffusion only, attr parity, grid parity, bounds fresh, SIR
+  // agent count): each key fixes every pointer and launch size the capture saw
+  std::map<std::tuple<int, int, int, int, int, size_t>, GraphEntry> graphs;
   Profiler prof;
   bool capturing = false;
   unsigned long long capture_kernels = 0;
@@ -284,6 +283,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     r.L = (int)Lu;
     r.nb = nb;
     r.Lb = (int)(Lu / nb);
+    r.invLb = 1.0f / (float)r.Lb;
     r.s = (int)std::llrint(p.sir_step * 1024.0);
     r.span = 2ull * (unsigned long long)r.s + 1ull;
     r.r2 = ru * ru;
@@ -295,20 +295,22 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     r.box_off = 0;
     const size_t nbox = (size_t)nb * nb * nb;
     s->box_capacity = nbox;
-    for (int h = 0; h < 2; ++h) {
-      if ((rc = dalloc_n(s, &s->sb.state[h].X, C)) || (rc = dalloc_n(s, &s->sb.state[h].Y, C)) ||
-          (rc = dalloc_n(s, &s->sb.state[h].Z, C)) || (rc = dalloc_n(s, &s->sb.state[h].st, C)))
-        return rc;
-    }
-    if ((rc = dalloc_n(s, &s->sb.key, C)) || (rc = dalloc_n(s, &s->sb.rank, C)) ||
-        (rc = dalloc_n(s, &s->sb.perm, C)) || (rc = dalloc_n(s, &s->sb.ninf, C)) ||
-        (rc = dalloc_n(s, &s->sb.count, nbox + 1)) || (rc = dalloc_n(s, &s->sb.start, nbox + 1)))
+    SirSingle& S = s->sb;
+    if ((rc = dalloc_n(s, &S.a.X, C)) || (rc = dalloc_n(s, &S.a.Y, C)) || (rc = dalloc_n(s, &S.a.Z, C)) ||
+        (rc = dalloc_n(s, &S.a.st, C)) || (rc = dalloc_n(s, &S.kn, C)) || (rc = dalloc_n(s, &S.rk, C)) ||
+        (rc = dalloc_n(s, &S.perm, C)) || (rc = dalloc_n(s, &S.ninf, C)) || (rc = dalloc_n(s, &S.box, C)) ||
+        (rc = dalloc_n(s, &S.src, C)) || (rc = dalloc_n(s, &S.count, nbox + 1)) ||
+        (rc = dalloc_n(s, &S.start, nbox + 1)))
       return rc;
-    s->sb.max_tiles = scan_tiles_for(nbox + 1);
-    if ((rc = dalloc_n(s, &s->sb.tiles, s->sb.max_tiles))) return rc;
-    CK(cudaMemsetAsync(s->sb.count, 0, sizeof(unsigned) * (nbox + 1), s->stream));
-    CK(cudaMemsetAsync(s->sb.ninf, 0, sizeof(unsigned) * C, s->stream));
-    CK(cudaMemsetAsync(s->sb.key, 0, sizeof(unsigned) * C, s->stream));
+    S.max_tiles = scan_tiles_for(nbox + 1);
+    if ((rc = dalloc_n(s, &S.tiles, S.max_tiles))) return rc;
+    // every index a step can read is in range from the start (see the bounds in the kernels)
+    CK(cudaMemsetAsync(S.count, 0, sizeof(unsigned) * (nbox + 1), s->stream));
+    CK(cudaMemsetAsync(S.start, 0, sizeof(unsigned) * (nbox + 1), s->stream));
+    CK(cudaMemsetAsync(S.perm, 0, sizeof(unsigned) * C, s->stream));
+    CK(cudaMemsetAsync(S.src, 0, sizeof(uint2) * C, s->stream));
+    CK(cudaMemsetAsync(S.ninf, 0, sizeof(unsigned) * C, s->stream));
+    CK(cudaMemsetAsync(S.box, 0, sizeof(unsigned) * C, s->stream));
     s->gh->nbox = (unsigned)nbox;
     s->gh->nbox1 = (unsigned)nbox + 1;
   } else {
@@ -489,8 +491,7 @@ int enqueue_mech_step(bdm_sim* s) {
 int enqueue_sir_step(bdm_sim* s) {
   SirSingle S = s->sb;
   S.run.agent_n = (unsigned)s->n_host;
-  RUN("sir_step", 5, launch_sir_step(s->stream, S, s->g, s->sir_par, s->blocks_stream, s->blocks_scan));
-  s->sir_par ^= 1;
+  RUN("sir_step", 5, launch_sir_step(s->stream, S, s->g, s->blocks_stream, s->blocks_scan));
   if (s->diffusion) return enqueue_diffusion(s);
   return BDM_OK;
 }
@@ -505,12 +506,12 @@ int enqueue_steps(bdm_sim* s, int n, bool diffusion_only) {
 
 int launch_steps(bdm_sim* s, int n, bool diffusion_only) {
   if (s->prof.on) return enqueue_steps(s, n, diffusion_only);
-  const auto key = std::make_tuple(n, (int)diffusion_only, s->attr_cur, s->grid_cur, s->sir_par,
+  const auto key = std::make_tuple(n, (int)diffusion_only, s->attr_cur, s->grid_cur,
                                    (int)s->bounds_fresh, s->is_sir ? s->n_host : (size_t)0);
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
     GraphEntry ge;
-    const int a0 = s->attr_cur, g0 = s->grid_cur, p0 = s->sir_par;
+    const int a0 = s->attr_cur, g0 = s->grid_cur;
     const bool f0 = s->bounds_fresh;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     s->capturing = true;
@@ -530,11 +531,9 @@ int launch_steps(bdm_sim* s, int n, bool diffusion_only) {
     ge.kernels = s->capture_kernels;
     ge.attr_cur = s->attr_cur;
     ge.grid_cur = s->grid_cur;
-    ge.sir_par = s->sir_par;
     ge.bounds_fresh = s->bounds_fresh;
     s->attr_cur = a0;
     s->grid_cur = g0;
-    s->sir_par = p0;
     s->bounds_fresh = f0;
     if (s->graphs.size() > 64) {
       for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -546,7 +545,6 @@ int launch_steps(bdm_sim* s, int n, bool diffusion_only) {
   g_launches += it->second.kernels;
   s->attr_cur = it->second.attr_cur;
   s->grid_cur = it->second.grid_cur;
-  s->sir_par = it->second.sir_par;
   s->bounds_fresh = it->second.bounds_fresh;
   return BDM_OK;
 }
@@ -639,17 +637,17 @@ int bdm_add_agents(bdm_sim* s, size_t n, const double* x, const double* y, const
         q[a * n + i] = (int)u;
       }
     }
-    const SirState& S = s->sb.state[s->sir_par];
+    if (sir_state)
+      for (size_t i = 0; i < n; ++i)
+        if (sir_state[i] > 2) return fail(s, BDM_EINVAL, "sir_state must be 0, 1 or 2");
+    const SirState& S = s->sb.a;
     CK(cudaMemcpyAsync(S.X + n0, q.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(S.Y + n0, q.data() + n, n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(S.Z + n0, q.data() + 2 * n, n * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (sir_state) {
-      for (size_t i = 0; i < n; ++i)
-        if (sir_state[i] > 2) return fail(s, BDM_EINVAL, "sir_state must be 0, 1 or 2");
-      CK(cudaMemcpyAsync(S.st + n0, sir_state, n, cudaMemcpyHostToDevice, st));
-    } else {
-      CK(cudaMemsetAsync(S.st + n0, 0, n, st));
-    }
+    if (sir_state) CK(cudaMemcpyAsync(S.st + n0, sir_state, n, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(S.st + n0, 0, n, st));
+    // boxes, ranks and histogram entries of the new agents for the coming step
+    RUN("sir_init", 1, launch_sir_init(st, s->sb, (unsigned)n0, (unsigned)(n0 + n), s->blocks_stream));
     s->n_host = n0 + n;
     CK(cudaStreamSynchronize(st));
     return BDM_OK;
@@ -713,7 +711,10 @@ int bdm_reset(bdm_sim* s) {
   s->gh->step = 0;
   s->gh->err = 0;
   s->gh->sir_counts[0] = s->gh->sir_counts[1] = s->gh->sir_counts[2] = 0;
+  s->gh->sir_sources = 0;
   CK(cudaMemcpy(s->g, s->gh, sizeof(DevGrid), cudaMemcpyHostToDevice));
+  // the SIR box histogram already holds the removed agents for their next step
+  if (s->is_sir) CK(cudaMemset(s->sb.count, 0, sizeof(unsigned) * (s->box_capacity + 1)));
   s->n_host = 0;
   s->poisoned = false;
   s->err_pending = false;
@@ -773,7 +774,7 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
   st->grid_box_q = G.Lq;
   cudaStream_t sm = s->stream;
   if (s->is_sir) {
-    const SirState& S = s->sb.state[s->sir_par];
+    const SirState& S = s->sb.a;
     if (n && (st->x || st->y || st->z)) {
       std::vector<int> q(n);
       int* src[3] = {S.X, S.Y, S.Z};
@@ -786,7 +787,7 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
     }
     if (n && st->sir_state) CK(cudaMemcpy(st->sir_state, S.st, n, cudaMemcpyDeviceToHost));
     if (n && st->neighbour_count) CK(cudaMemcpy(st->neighbour_count, s->sb.ninf, n * sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (n && st->box_id) CK(cudaMemcpy(st->box_id, s->sb.key, n * sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (n && st->box_id) CK(cudaMemcpy(st->box_id, s->sb.box, n * sizeof(unsigned), cudaMemcpyDeviceToHost));
   } else if (n && (st->x || st->y || st->z || st->diameter || st->volume || st->neighbour_count || st->box_id)) {
     MechBuffers& b = s->mb;
     const AgentArrays A = b.attr[s->attr_cur];

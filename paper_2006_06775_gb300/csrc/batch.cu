@@ -4,7 +4,8 @@
 // The runs keep their own parameters (BioDynaMo, arXiv 2006.06775, Sec. "Epidemiology use case":
 // infection radius and probability, recovery probability, movement bound) and their own agents, in
 // concatenated arrays with per-run offsets.  A work list of (run, 256-agent tile) pairs lets one
-// persistent grid cover every run; its phases (box ids + histogram, scan, scatter, update) are
+// persistent grid cover every run; its phases (scan of the box histogram, box order and infected
+// list, push of infected agents into their neighbours' counts, update with the next histogram) are
 // separated by a grid barrier whose waits are bounded.  Every run computes exactly what it would
 // compute alone: the arithmetic is integer and per run.
 #include <cuda_runtime.h>
@@ -43,8 +44,7 @@ struct bdm_batch {
   SirBatchDev dev{};
   DevGrid* g = nullptr;
   DevGrid* gh = nullptr;
-  // n-step graphs; a step reads its buffer parity from the device step counter, so one graph
-  // per n serves every starting step
+  // n-step graphs; every step uses the same buffers, so one graph per n serves every starting step
   std::map<int, cudaGraphExec_t> graphs;
   unsigned long long steps_done = 0;
   void* (*alloc)(size_t, void*) = nullptr;
@@ -108,6 +108,7 @@ int build(bdm_batch* b) {
     s.L = (int)L;
     s.nb = nb;
     s.Lb = (int)(L / nb);
+    s.invLb = 1.0f / (float)s.Lb;
     s.s = (int)std::llrint(p.sir_step * 1024.0);
     s.span = 2ull * (unsigned long long)s.s + 1ull;
     s.r2 = r * r;
@@ -129,15 +130,15 @@ int build(bdm_batch* b) {
   SirBatchDev& D = b->dev;
   const size_t A = std::max<size_t>(total, 1);
   int rc;
-  for (int h = 0; h < 2; ++h)
-    if ((rc = balloc_n(b, &D.state[h].X, A)) || (rc = balloc_n(b, &D.state[h].Y, A)) ||
-        (rc = balloc_n(b, &D.state[h].Z, A)) || (rc = balloc_n(b, &D.state[h].st, A)))
-      return rc;
+  if ((rc = balloc_n(b, &D.a.X, A)) || (rc = balloc_n(b, &D.a.Y, A)) || (rc = balloc_n(b, &D.a.Z, A)) ||
+      (rc = balloc_n(b, &D.a.st, A)))
+    return rc;
   D.max_tiles = (unsigned)((boxes + 1 + kScanTile - 1) / kScanTile + 1);
   SirRun* druns = nullptr;
   unsigned *dtr = nullptr, *dts = nullptr;
-  if ((rc = balloc_n(b, &D.key, A)) || (rc = balloc_n(b, &D.rank, A)) ||
+  if ((rc = balloc_n(b, &D.kn, A)) || (rc = balloc_n(b, &D.rk, A)) ||
       (rc = balloc_n(b, &D.perm, A)) || (rc = balloc_n(b, &D.ninf, A)) ||
+      (rc = balloc_n(b, &D.box, A)) || (rc = balloc_n(b, &D.src, A)) ||
       (rc = balloc_n(b, &D.count, boxes + 1)) || (rc = balloc_n(b, &D.start, boxes + 1)) ||
       (rc = balloc_n(b, &D.tiles, D.max_tiles)) || (rc = balloc_n(b, &druns, (size_t)R)) ||
       (rc = balloc_n(b, &dtr, std::max<size_t>(tile_run.size(), 1))) ||
@@ -149,29 +150,28 @@ int build(bdm_batch* b) {
   for (int k = 0; k < R; ++k) {
     const size_t n = b->hX[k].size(), off = b->runs[k].agent_off;
     if (!n) continue;
-    BCK(cudaMemcpyAsync(D.state[0].X + off, b->hX[k].data(), n * 4, cudaMemcpyHostToDevice, s));
-    BCK(cudaMemcpyAsync(D.state[0].Y + off, b->hY[k].data(), n * 4, cudaMemcpyHostToDevice, s));
-    BCK(cudaMemcpyAsync(D.state[0].Z + off, b->hZ[k].data(), n * 4, cudaMemcpyHostToDevice, s));
-    BCK(cudaMemcpyAsync(D.state[0].st + off, b->hS[k].data(), n, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(D.a.X + off, b->hX[k].data(), n * 4, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(D.a.Y + off, b->hY[k].data(), n * 4, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(D.a.Z + off, b->hZ[k].data(), n * 4, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(D.a.st + off, b->hS[k].data(), n, cudaMemcpyHostToDevice, s));
   }
   BCK(cudaMemcpyAsync(druns, b->runs.data(), sizeof(SirRun) * R, cudaMemcpyHostToDevice, s));
   if (!tile_run.empty()) {
     BCK(cudaMemcpyAsync(dtr, tile_run.data(), 4 * tile_run.size(), cudaMemcpyHostToDevice, s));
     BCK(cudaMemcpyAsync(dts, tile_start.data(), 4 * tile_start.size(), cudaMemcpyHostToDevice, s));
   }
-  // start/perm are zeroed so that every index a step can read is in range even when a bounded
+  // start/perm/src are zeroed so that every index a step can read is in range even when a bounded
   // barrier wait gives up before the phase that writes them has finished
   BCK(cudaMemsetAsync(D.count, 0, 4 * (boxes + 1), s));
   BCK(cudaMemsetAsync(D.start, 0, 4 * (boxes + 1), s));
   BCK(cudaMemsetAsync(D.perm, 0, 4 * A, s));
+  BCK(cudaMemsetAsync(D.src, 0, 8 * A, s));
   BCK(cudaMemsetAsync(D.ninf, 0, 4 * A, s));
-  BCK(cudaMemsetAsync(D.key, 0, 4 * A, s));
   BCK(cudaMemsetAsync(D.hist, 0, 4 * (size_t)b->hist_len * R * 3, s));
   BCK(cudaMemsetAsync(D.bar, 0, 8, s));
   BCK(cudaMallocHost((void**)&b->gh, sizeof(DevGrid)));
   std::memset(b->gh, 0, sizeof(DevGrid));
   BCK(cudaMemcpyAsync(b->g, b->gh, sizeof(DevGrid), cudaMemcpyHostToDevice, s));
-  BCK(cudaStreamSynchronize(s));
   D.run = druns;
   D.tile_run = dtr;
   D.tile_start = dts;
@@ -186,6 +186,11 @@ int build(bdm_batch* b) {
   const int per_sm = sir_ensemble_blocks_per_sm();
   if (per_sm < 1) return bfail(b, BDM_ECUDA, "persistent SIR kernel cannot be resident");
   b->blocks = sms * per_sm;
+  // boxes, ranks and histogram of the first step
+  launch_sir_init_batch(s, D, b->blocks);
+  BCK(cudaGetLastError());
+  bdm_count_launches(1);
+  BCK(cudaStreamSynchronize(s));
   b->built = true;
   return BDM_OK;
 }
@@ -342,8 +347,7 @@ int bdm_batch_get_state(bdm_batch* b, int sim, bdm_state* st) {
   if (rc) return rc;
   const SirRun& r = b->runs[sim];
   const size_t n = r.agent_n, off = r.agent_off;
-  const int par = (int)(b->gh->step & 1ull);
-  const SirState& S = b->dev.state[par];
+  const SirState& S = b->dev.a;
   st->n = n;
   st->step = b->gh->step;
   st->mass_total = 0.0;
@@ -367,7 +371,7 @@ int bdm_batch_get_state(bdm_batch* b, int sim, bdm_state* st) {
   if (n && st->sir_state) BCK(cudaMemcpy(st->sir_state, S.st + off, n, cudaMemcpyDeviceToHost));
   if (n && st->neighbour_count) BCK(cudaMemcpy(st->neighbour_count, b->dev.ninf + off, n * 4, cudaMemcpyDeviceToHost));
   if (n && st->box_id) {
-    BCK(cudaMemcpy(st->box_id, b->dev.key + off, n * 4, cudaMemcpyDeviceToHost));
+    BCK(cudaMemcpy(st->box_id, b->dev.box + off, n * 4, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < n; ++i) st->box_id[i] -= r.box_off;  // run-local box id
   }
   return BDM_OK;

@@ -52,6 +52,7 @@ struct DevGrid {
   unsigned scan_ctr[2];           // dynamic tile counters of the two scans
   unsigned err;                   // ErrBit flags
   unsigned sir_counts[3];         // S, I, R after the last SIR step
+  unsigned sir_sources;           // entries of this SIR step's list of infected agents
   unsigned long long step;        // steps completed (Philox counters)
   unsigned bad_input;             // first rejected agent of the last upload (~0u: none)
   double mass;                    // FP64 substance total after the last diffusion step

@@ -5,32 +5,72 @@
 // Reading R10: synchronous integer step on a 2^-10 um lattice, periodic cube, Philox4x32-10 keyed
 // by (seed, run) with counters (id, step, stream, 0).
 //
-// Agents stay in id order.  Every agent's box id is computed each step, and the uniform grid index
-// (box -> agent ids, rebuilt by counting sort) holds the INFECTED agents only: the infection rule and
-// the infected-neighbour count only ever look at infected agents, so searching the 27 boxes of this
-// index gives exactly the counts of a full index at a fraction of the candidates.  One run uses four
-// kernels per step; a batch of runs uses ONE persistent kernel per step whose phases are separated
-// by a bounded grid barrier.
+// Agents stay in id order and are updated in place.  A step is:
+//   scan     exclusive scan of the box histogram (built by the previous step's update)
+//   index    agents into box order (perm); infected agents into a compact source list
+//   push     every infected agent visits the agents of its 27 boxes and adds 1 to the infected-
+//            neighbour count of each one within the radius (minimum image)
+//   update   infection / recovery / move of every agent from its count, and the next step's box,
+//            rank and histogram entry
+// Only the few infected agents search the grid, so the per-agent work is a handful of streaming
+// accesses and two Philox blocks.  The counts are integer sums, so the order of the atomic
+// additions does not matter and every result equals the pull-form definition exactly.  One run
+// uses four kernels per step; a batch of runs uses ONE persistent kernel per step whose phases
+// are separated by a bounded grid barrier.
 #include "common.cuh"
 #include "scan.cuh"
 #include "sir.cuh"
 
 namespace bdm {
 
-__device__ __forceinline__ unsigned sir_box(int X, int Y, int Z, const SirRun& r) {
-  return (unsigned)(X / r.Lb) + (unsigned)r.nb * ((unsigned)(Y / r.Lb) + (unsigned)r.nb * (unsigned)(Z / r.Lb));
+// floor(X / Lb) for 0 <= X < L < 2^31 and at most 1625 boxes per axis: the float estimate is within
+// one of the quotient (relative error ~3 * 2^-24), one integer comparison makes it exact.
+__device__ __forceinline__ int box_coord(int X, const SirRun& r) {
+  int q = __float2int_rz(__int2float_rn(X) * r.invLb);
+  const int t = q * r.Lb;
+  if (t > X) --q;
+  else if (X - t >= r.Lb) ++q;
+  return q;
 }
 
-__device__ __forceinline__ int neighbour_boxes(int b, int nb, int out[3]) {
+__device__ __forceinline__ unsigned sir_box(int X, int Y, int Z, const SirRun& r) {
+  return (unsigned)box_coord(X, r) +
+         (unsigned)r.nb * ((unsigned)box_coord(Y, r) + (unsigned)r.nb * (unsigned)box_coord(Z, r));
+}
+
+// Distinct periodic neighbours {c, c+1, c-1} of box coordinate c on an axis of nb boxes.
+__device__ __forceinline__ int neighbour_boxes(int c, int nb, int out[3]) {
   if (nb == 1) {
     out[0] = 0;
     return 1;
   }
-  out[0] = b;
-  out[1] = (b + 1) % nb;
+  out[0] = c;
+  out[1] = (c + 1) % nb;
   if (nb == 2) return 2;
-  out[2] = (b + nb - 1) % nb;
+  out[2] = (c + nb - 1) % nb;
   return 3;
+}
+
+// The x-neighbours of box coordinate c as at most two half-open runs of consecutive boxes.
+__device__ __forceinline__ int neighbour_runs(int c, int nb, int lo[2], int hi[2]) {
+  if (nb <= 3) {
+    lo[0] = 0;
+    hi[0] = nb;
+    return 1;
+  }
+  if (c == 0) {
+    lo[0] = 0, hi[0] = 2;
+    lo[1] = nb - 1, hi[1] = nb;
+    return 2;
+  }
+  if (c == nb - 1) {
+    lo[0] = 0, hi[0] = 1;
+    lo[1] = nb - 2, hi[1] = nb;
+    return 2;
+  }
+  lo[0] = c - 1;
+  hi[0] = c + 2;
+  return 1;
 }
 
 __device__ __forceinline__ long long min_image(long long d, long long L) {
@@ -39,42 +79,84 @@ __device__ __forceinline__ long long min_image(long long d, long long L) {
   return d;
 }
 
-// Update of agent a (global index; id within its run = a - r.agent_off).  Returns the new state.
-__device__ __forceinline__ unsigned char sir_update(unsigned a, const SirRun& r, const SirState cur,
-                                                    SirState nxt, const unsigned* __restrict__ start,
-                                                    const unsigned* __restrict__ perm,
-                                                    unsigned* __restrict__ ninf, unsigned step) {
-  const int Xi = cur.X[a], Yi = cur.Y[a], Zi = cur.Z[a];
-  const unsigned char si = cur.st[a];
+// index phase for agent p of run ri (every lane of the warp calls; `valid` masks padding): place p
+// in box order, clear its count, and append it to the source list if infected.  The bounds keep a
+// step whose scan or barrier was cut short by a timeout inside the arrays.
+__device__ __forceinline__ void sir_index(unsigned p, bool valid, unsigned ri, const SirState a,
+                                          const unsigned* __restrict__ kn,
+                                          const unsigned* __restrict__ rk,
+                                          const unsigned* __restrict__ start,
+                                          unsigned* __restrict__ perm, unsigned* __restrict__ ninf,
+                                          uint2* __restrict__ src, unsigned* nsrc, unsigned total) {
+  bool inf = false;
+  if (valid) {
+    const unsigned d = start[kn[p]] + rk[p];
+    if (d < total) perm[d] = p;
+    ninf[p] = 0u;
+    inf = a.st[p] == 1;
+  }
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, inf);
+  if (m) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(nsrc, (unsigned)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    const unsigned k = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+    if (inf && k < total) src[k] = make_uint2(p, ri);
+  }
+}
+
+// push phase for infected agent j of run r.
+__device__ __forceinline__ void sir_push(unsigned j, const SirRun& r, const SirState a,
+                                         const unsigned* __restrict__ start,
+                                         const unsigned* __restrict__ perm,
+                                         unsigned* __restrict__ ninf, unsigned total) {
+  const int Xj = a.X[j], Yj = a.Y[j], Zj = a.Z[j];
   const long long L = r.L;
-  int cx[3], cy[3], cz[3];
-  const int nx = neighbour_boxes(Xi / r.Lb, r.nb, cx);
-  const int ny = neighbour_boxes(Yi / r.Lb, r.nb, cy);
-  const int nz = neighbour_boxes(Zi / r.Lb, r.nb, cz);
-  unsigned cnt = 0;
+  const int nb = r.nb;
+  int cy[3], cz[3], xlo[2], xhi[2];
+  const int ny = neighbour_boxes(box_coord(Yj, r), nb, cy);
+  const int nz = neighbour_boxes(box_coord(Zj, r), nb, cz);
+  const int nr = neighbour_runs(box_coord(Xj, r), nb, xlo, xhi);
   for (int qz = 0; qz < nz; ++qz)
-    for (int qy = 0; qy < ny; ++qy)
-      for (int qx = 0; qx < nx; ++qx) {
-        const unsigned b = r.box_off + (unsigned)cx[qx] +
-                           (unsigned)r.nb * ((unsigned)cy[qy] + (unsigned)r.nb * (unsigned)cz[qz]);
-        const unsigned e = start[b + 1];
-        for (unsigned m = start[b]; m < e; ++m) {
-          const unsigned j = perm[m];  // an infected agent
-          if (j == a) continue;
-          const long long dx = min_image((long long)Xi - cur.X[j], L);
-          const long long dy = min_image((long long)Yi - cur.Y[j], L);
-          const long long dz = min_image((long long)Zi - cur.Z[j], L);
-          cnt += (dx * dx + dy * dy + dz * dz < r.r2) ? 1u : 0u;
+    for (int qy = 0; qy < ny; ++qy) {
+      const unsigned row = r.box_off + (unsigned)nb * ((unsigned)cy[qy] + (unsigned)nb * (unsigned)cz[qz]);
+      for (int k = 0; k < nr; ++k) {
+        const unsigned m0 = start[row + (unsigned)xlo[k]];
+        const unsigned m1 = min(start[row + (unsigned)xhi[k]], total);
+        for (unsigned m = m0; m < m1; ++m) {
+          const unsigned i = perm[m];
+          if (i == j || i >= total) continue;
+          const long long dx = min_image((long long)a.X[i] - Xj, L);
+          const long long dy = min_image((long long)a.Y[i] - Yj, L);
+          const long long dz = min_image((long long)a.Z[i] - Zj, L);
+          if (dx * dx + dy * dy + dz * dz < r.r2) atomicAdd(&ninf[i], 1u);
         }
       }
-  const unsigned id = a - r.agent_off;
-  const uint4 w = philox10(make_uint4(id, step, 0u, 0u), r.key);
+    }
+}
+
+// update phase for agent p of run r: draws, move, read-outs, next box / rank / histogram entry.
+__device__ __forceinline__ unsigned char sir_update(unsigned p, const SirRun& r, SirState a,
+                                                    const unsigned* __restrict__ ninf,
+                                                    unsigned* __restrict__ box,
+                                                    unsigned* __restrict__ kn,
+                                                    unsigned* __restrict__ rk,
+                                                    unsigned* __restrict__ count, unsigned step) {
+  const int P[3] = {a.X[p], a.Y[p], a.Z[p]};
+  const unsigned char si = a.st[p];
+  const unsigned id = p - r.agent_off;
+  const unsigned cnt = ninf[p];
   unsigned char ns = si;
-  if (si == 0 && cnt > 0 && (unsigned long long)w.x < r.thr_inf) ns = 1;
-  if (si == 1 && (unsigned long long)w.y < r.thr_rec) ns = 2;
+  if ((si == 0 && cnt > 0) || si == 1) {  // the only cases in which this draw decides anything
+    const uint4 w = philox10(make_uint4(id, step, 0u, 0u), r.key);
+    if (si == 0 && (unsigned long long)w.x < r.thr_inf) ns = 1;
+    if (si == 1 && (unsigned long long)w.y < r.thr_rec) ns = 2;
+  }
   const uint4 mv = philox10(make_uint4(id, step, 1u, 0u), r.key);
-  const int P[3] = {Xi, Yi, Zi};
   const unsigned W[3] = {mv.x, mv.y, mv.z};
+  const long long L = r.L;
   int NP[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -83,11 +165,14 @@ __device__ __forceinline__ unsigned char sir_update(unsigned a, const SirRun& r,
     else if (v >= L) v -= L;
     NP[k] = (int)v;
   }
-  nxt.X[a] = NP[0];
-  nxt.Y[a] = NP[1];
-  nxt.Z[a] = NP[2];
-  nxt.st[a] = ns;
-  ninf[a] = cnt;
+  a.X[p] = NP[0];
+  a.Y[p] = NP[1];
+  a.Z[p] = NP[2];
+  a.st[p] = ns;
+  box[p] = kn[p];
+  const unsigned b2 = r.box_off + sir_box(NP[0], NP[1], NP[2], r);
+  kn[p] = b2;
+  rk[p] = atomicAdd(&count[b2], 1u);
   return ns;
 }
 
@@ -105,45 +190,61 @@ __device__ __forceinline__ void commit_counts(unsigned char ns, bool valid, unsi
   if (threadIdx.x < 3 && s_c[threadIdx.x]) atomicAdd(&dst[threadIdx.x], s_c[threadIdx.x]);
 }
 
-// ---- one run: keyhist -> scan -> scatter -> update ------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_sir_keyhist(SirState cur, unsigned* __restrict__ key,
-                                                        unsigned* __restrict__ rank,
-                                                        unsigned* __restrict__ count, SirRun r,
-                                                        DevGrid* g) {
-  const unsigned n = r.agent_n;
-  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid == 0) {
+// ---- one run: [init] ; scan -> index -> push -> update ---------------------------------------
+__global__ void __launch_bounds__(kBlock) k_sir_init(SirState a, unsigned* __restrict__ kn,
+                                                     unsigned* __restrict__ rk,
+                                                     unsigned* __restrict__ box,
+                                                     unsigned* __restrict__ count, SirRun r,
+                                                     unsigned lo, unsigned hi) {
+  for (unsigned p = lo + blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x) {
+    const unsigned b = r.box_off + sir_box(a.X[p], a.Y[p], a.Z[p], r);
+    kn[p] = b;
+    box[p] = b;
+    rk[p] = atomicAdd(&count[b], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sir_index(SirState a, const unsigned* __restrict__ kn,
+                                                      const unsigned* __restrict__ rk,
+                                                      const unsigned* __restrict__ start,
+                                                      unsigned* __restrict__ perm,
+                                                      unsigned* __restrict__ ninf,
+                                                      uint2* __restrict__ src, unsigned n,
+                                                      DevGrid* g) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the scan has finished: ready its counter
     g->scan_ctr[0] = 0;
     g->sir_counts[0] = g->sir_counts[1] = g->sir_counts[2] = 0;
   }
-  for (unsigned a = tid; a < n; a += gridDim.x * blockDim.x) {
-    const unsigned b = sir_box(cur.X[a], cur.Y[a], cur.Z[a], r);
-    key[a] = b;
-    if (cur.st[a] == 1) rank[a] = atomicAdd(&count[b], 1u);
+  for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const unsigned p = base + threadIdx.x;
+    sir_index(p, p < n, 0u, a, kn, rk, start, perm, ninf, src, &g->sir_sources, n);
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_sir_scatter(const unsigned* __restrict__ key,
-                                                        const unsigned* __restrict__ rank,
-                                                        const unsigned char* __restrict__ st,
-                                                        const unsigned* __restrict__ start,
-                                                        unsigned* __restrict__ perm, unsigned n) {
-  for (unsigned a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x)
-    if (st[a] == 1) perm[start[key[a]] + rank[a]] = a;
+__global__ void __launch_bounds__(kBlock) k_sir_push(SirState a, const unsigned* __restrict__ start,
+                                                     const unsigned* __restrict__ perm,
+                                                     unsigned* __restrict__ ninf,
+                                                     const uint2* __restrict__ src, SirRun r,
+                                                     unsigned n, const DevGrid* g) {
+  const unsigned ns = min(g->sir_sources, n);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x)
+    sir_push(src[i].x, r, a, start, perm, ninf, n);
 }
 
-__global__ void __launch_bounds__(kBlock) k_sir_update(SirState cur, SirState nxt,
-                                                       const unsigned* __restrict__ start,
-                                                       const unsigned* __restrict__ perm,
-                                                       unsigned* __restrict__ ninf, SirRun r,
+__global__ void __launch_bounds__(kBlock) k_sir_update(SirState a, const unsigned* __restrict__ ninf,
+                                                       unsigned* __restrict__ box,
+                                                       unsigned* __restrict__ kn,
+                                                       unsigned* __restrict__ rk,
+                                                       unsigned* __restrict__ count, SirRun r,
                                                        DevGrid* g) {
   const unsigned n = r.agent_n;
   const unsigned step = (unsigned)g->step;
+  if (blockIdx.x == 0 && threadIdx.x == 0) g->sir_sources = 0;  // the push has read it
   for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const unsigned a = base + threadIdx.x;
+    const unsigned p = base + threadIdx.x;
     unsigned char ns = 0;
-    if (a < n) ns = sir_update(a, r, cur, nxt, start, perm, ninf, step);
-    commit_counts(ns, a < n, g->sir_counts);
+    if (p < n) ns = sir_update(p, r, a, ninf, box, kn, rk, count, step);
+    commit_counts(ns, p < n, g->sir_counts);
   }
 }
 
@@ -176,45 +277,65 @@ __device__ __forceinline__ void grid_barrier(unsigned* ctr, volatile unsigned* g
   __syncthreads();
 }
 
+__global__ void __launch_bounds__(kBlock) k_sir_init_batch(SirBatchDev B) {
+  for (unsigned t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+    const SirRun r = B.run[B.tile_run[t]];
+    const unsigned p = B.tile_start[t] + threadIdx.x;
+    if (p < r.agent_off + r.agent_n) {
+      const unsigned b = r.box_off + sir_box(B.a.X[p], B.a.Y[p], B.a.Z[p], r);
+      B.kn[p] = b;
+      B.box[p] = b;
+      B.rk[p] = atomicAdd(&B.count[b], 1u);
+    }
+  }
+}
+
+// On entry: the histogram of the agents' boxes is in `count`; the scan's tile flags, its counter
+// and the source counter are zero.
 __global__ void __launch_bounds__(kBlock) k_sir_ensemble(SirBatchDev B, DevGrid* g,
                                                           unsigned barrier_blocks,
                                                           unsigned spin_limit) {
   const unsigned step = (unsigned)g->step;
-  const int par = (int)(g->step & 1ull);
-  const SirState cur = B.state[par], nxt = B.state[par ^ 1];
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
-  // P1: reset the scan and this step's count slot; box id + histogram
-  for (unsigned t = tid; t < B.max_tiles; t += nthreads) B.tiles[t] = 0ull;
   unsigned* slot = B.hist + (size_t)(step % B.hist_len) * B.runs * 3u;
-  for (unsigned t = tid; t < B.runs * 3u; t += nthreads) slot[t] = 0u;
-  if (tid == 0) g->scan_ctr[0] = 0u;
-  for (unsigned t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
-    const SirRun r = B.run[B.tile_run[t]];
-    const unsigned a = B.tile_start[t] + threadIdx.x;
-    if (a < r.agent_off + r.agent_n) {
-      const unsigned b = r.box_off + sir_box(cur.X[a], cur.Y[a], cur.Z[a], r);
-      B.key[a] = b;
-      if (cur.st[a] == 1) B.rank[a] = atomicAdd(&B.count[b], 1u);
-    }
-  }
-  grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
-  if (tid == 0) g->step += 1ull;  // every block read the step before the barrier
-  // P2: global exclusive scan over all runs' boxes (clears the histogram)
+  // P1: global exclusive scan over all runs' boxes (clears the histogram)
   scan_tiles(B.count, B.start, B.total_boxes + 1u, B.tiles, &g->scan_ctr[0], &g->err, 1);
   grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
-  // P3: scatter agent indices into box order
-  for (unsigned a = tid; a < B.total_agents; a += nthreads)
-    if (cur.st[a] == 1) B.perm[B.start[B.key[a]] + B.rank[a]] = a;
-  grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
-  // P4: infection, recovery, move; per-run S/I/R counts of this step
+  // every block read the step before the barrier; the scan's flags are free again
+  if (tid == 0) {
+    g->step += 1ull;
+    g->scan_ctr[0] = 0u;
+  }
+  for (unsigned t = tid; t < B.max_tiles; t += nthreads) B.tiles[t] = 0ull;
+  for (unsigned t = tid; t < B.runs * 3u; t += nthreads) slot[t] = 0u;
+  // P2: box order and source list
   for (unsigned t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
     const unsigned ri = B.tile_run[t];
     const SirRun r = B.run[ri];
-    const unsigned a = B.tile_start[t] + threadIdx.x;
-    const bool valid = a < r.agent_off + r.agent_n;
+    const unsigned p = B.tile_start[t] + threadIdx.x;
+    sir_index(p, p < r.agent_off + r.agent_n, ri, B.a, B.kn, B.rk, B.start, B.perm, B.ninf, B.src,
+              &g->sir_sources, B.total_agents);
+  }
+  grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
+  // P3: infected agents push into their neighbours' counts
+  {
+    const unsigned ns = min(*(volatile unsigned*)&g->sir_sources, B.total_agents);
+    for (unsigned i = tid; i < ns; i += nthreads) {
+      const uint2 e = B.src[i];
+      sir_push(e.x, B.run[e.y < B.runs ? e.y : 0u], B.a, B.start, B.perm, B.ninf, B.total_agents);
+    }
+  }
+  grid_barrier(&B.bar[0], &B.bar[1], barrier_blocks, &g->err, spin_limit);
+  if (tid == 0) g->sir_sources = 0u;  // every block has read it
+  // P4: infection, recovery, move, next histogram; per-run S/I/R counts of this step
+  for (unsigned t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+    const unsigned ri = B.tile_run[t];
+    const SirRun r = B.run[ri];
+    const unsigned p = B.tile_start[t] + threadIdx.x;
+    const bool valid = p < r.agent_off + r.agent_n;
     unsigned char ns = 0;
-    if (valid) ns = sir_update(a, r, cur, nxt, B.start, B.perm, B.ninf, step);
+    if (valid) ns = sir_update(p, r, B.a, B.ninf, B.box, B.kn, B.rk, B.count, step);
     commit_counts(ns, valid, slot + 3u * ri);
   }
 }
@@ -232,14 +353,25 @@ void launch_philox(cudaStream_t s, unsigned n, const uint4* ctr, const uint2* ke
   k_philox<<<blocks < 4096u ? blocks : 4096u, kBlock, 0, s>>>(n, ctr, key, out);
 }
 
-void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int par, int grid_blocks,
-                     int scan_blocks) {
-  const SirState cur = S.state[par], nxt = S.state[par ^ 1];
-  k_sir_keyhist<<<grid_blocks, kBlock, 0, s>>>(cur, S.key, S.rank, S.count, S.run, g);
+void launch_sir_init(cudaStream_t s, const SirSingle& S, unsigned lo, unsigned hi, int grid_blocks) {
+  if (hi <= lo) return;
+  const unsigned need = (hi - lo + kBlock - 1) / kBlock;
+  k_sir_init<<<need < (unsigned)grid_blocks ? need : (unsigned)grid_blocks, kBlock, 0, s>>>(
+      S.a, S.kn, S.rk, S.box, S.count, S.run, lo, hi);
+}
+
+void launch_sir_init_batch(cudaStream_t s, const SirBatchDev& B, int grid_blocks) {
+  if (!B.ntiles) return;
+  k_sir_init_batch<<<B.ntiles < (unsigned)grid_blocks ? B.ntiles : (unsigned)grid_blocks, kBlock, 0, s>>>(B);
+}
+
+void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int grid_blocks, int scan_blocks) {
+  const unsigned n = S.run.agent_n;
   cudaMemsetAsync(S.tiles, 0, sizeof(unsigned long long) * S.max_tiles, s);
   launch_scan(s, S.count, S.start, &g->nbox1, S.tiles, &g->scan_ctr[0], &g->err, 1, scan_blocks);
-  k_sir_scatter<<<grid_blocks, kBlock, 0, s>>>(S.key, S.rank, cur.st, S.start, S.perm, S.run.agent_n);
-  k_sir_update<<<grid_blocks, kBlock, 0, s>>>(cur, nxt, S.start, S.perm, S.ninf, S.run, g);
+  k_sir_index<<<grid_blocks, kBlock, 0, s>>>(S.a, S.kn, S.rk, S.start, S.perm, S.ninf, S.src, n, g);
+  k_sir_push<<<grid_blocks, kBlock, 0, s>>>(S.a, S.start, S.perm, S.ninf, S.src, S.run, n, g);
+  k_sir_update<<<grid_blocks, kBlock, 0, s>>>(S.a, S.ninf, S.box, S.kn, S.rk, S.count, S.run, g);
   launch_step_done(s, g);
 }
 

@@ -9,6 +9,7 @@ struct SirRun {
   int L;                        // periodic cube side
   int nb;                       // boxes per axis
   int Lb;                       // box side = L / nb (>= r)
+  float invLb;                  // float(1 / Lb): estimate for the box division
   int s;                        // move bound per axis
   unsigned long long span;      // 2 s + 1
   long long r2;                 // infection radius squared
@@ -19,22 +20,32 @@ struct SirRun {
   unsigned box_off;             // boxes of this run: [box_off, box_off + nb^3)
 };
 
-struct SirState {               // one ping-pong half, agents in id order
+// The agents, in id order, updated in place.
+struct SirState {
   int *X, *Y, *Z;
   unsigned char* st;
 };
 
+// Per-agent and per-box buffers (one run, or a batch of concatenated runs):
+//   kn/rk   box of each agent at the start of the coming step (global box index) and its rank in
+//           that box; the update writes them together with the box histogram `count`
+//   perm    agents in box order (start[box] .. start[box + 1])
+//   src     this step's infected agents as (agent, run)
+//   ninf    infected agents within the radius of each agent (read-out and infection input)
+//   box     read-out: box of each agent at the start of the last step
 struct SirSingle {
-  SirState state[2];
-  unsigned *key, *rank, *perm, *count, *start, *ninf;
+  SirState a;
+  unsigned *kn, *rk, *perm, *count, *start, *ninf, *box;
+  uint2* src;
   unsigned long long* tiles;
   unsigned max_tiles;
   SirRun run;
 };
 
 struct SirBatchDev {
-  SirState state[2];
-  unsigned *key, *rank, *perm, *count, *start, *ninf;
+  SirState a;
+  unsigned *kn, *rk, *perm, *count, *start, *ninf, *box;
+  uint2* src;
   unsigned long long* tiles;
   unsigned max_tiles;
   const SirRun* run;            // [runs]
@@ -59,8 +70,11 @@ inline int sir_box_count(long long L, long long r, int given, size_t n) {
   return 1;
 }
 
-void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int par, int grid_blocks,
-                     int scan_blocks);
+// Box, rank and histogram entry of agents [lo, hi) of a single run before their first step.
+void launch_sir_init(cudaStream_t s, const SirSingle& S, unsigned lo, unsigned hi, int grid_blocks);
+// Same for every agent of a batch.
+void launch_sir_init_batch(cudaStream_t s, const SirBatchDev& B, int grid_blocks);
+void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int grid_blocks, int scan_blocks);
 cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g, int blocks,
                                 unsigned barrier_extra, unsigned spin_limit, bool cooperative);
 int sir_ensemble_blocks_per_sm();

@@ -21,7 +21,7 @@ import numpy as np
 from . import synth
 
 MECH_BYTES_PER_AGENT = 124 + 8 * 3   # agent arrays + ~3 boxes per agent (count/start, capacity)
-SIR_BYTES_PER_AGENT = 2 * 13 + 16 + 8
+SIR_BYTES_PER_AGENT = 13 + 5 * 4 + 8 + 8   # state, 5 words per agent, list entry, ~1 box each
 MIN_BYTES = 4 << 20
 
 

@@ -116,13 +116,13 @@ def tune_mechanics(params, inputs, volume, cache=None, measure=None, candidates=
 
 
 def sir_box_candidates(params, n):
-    """Divisors of the lattice side near (0.6 .. 1.5) x n^(1/3) with box side >= r."""
+    """Divisors of the lattice side near (0.5 .. 2) x n^(1/3) with box side >= r."""
     L = int(round(params["sir_domain"] * 1024))
     r = int(round(params["sir_radius"] * 1024))
     hi = L // r if r > 0 else L
     out = set()
     base = max(1.0, n ** (1.0 / 3.0))
-    for f in (0.6, 0.8, 1.0, 1.25, 1.5):
+    for f in (0.5, 0.7, 1.0, 1.25, 1.5, 2.0):
         t = min(hi, max(1, int(base * f)))
         for nb in range(t, 0, -1):
             if L % nb == 0:
