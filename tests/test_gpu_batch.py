@@ -15,14 +15,15 @@ FIELDS = ("x", "y", "z", "sir_state", "neighbour_count", "box_id")
 def uneven_runs():
     """Runs of different sizes, domains, box counts and probabilities."""
     out = []
-    specs = [(5000, 400.0, 16), (1, 50.0, 2), (3000, 150.0, 3), (20000, 1000.0, 0),
-             (700, 100.0, 1), (12000, 600.0, 0)]
+    specs = [(5000, 400.0, 16, 0.05), (1, 50.0, 2, 0.05), (3000, 150.0, 3, 0.05),
+             (20000, 1000.0, 0, 0.05), (700, 100.0, 1, 0.05), (12000, 600.0, 0, 0.05),
+             (2500, 90.0, 6, 0.6)]
     g = synth.rng(7, 7)
-    for k, (n, dom, nb) in enumerate(specs):
+    for k, (n, dom, nb, frac) in enumerate(specs):
         p = dict(kind="sir", seed=3, run_id=k, sir_domain=dom, sir_radius=6.0, sir_step=5.0,
                  sir_boxes=nb, p_infect=float(g.uniform(0.1, 0.4)),
                  p_recover=float(g.uniform(0.01, 0.03)))
-        x, y, z, st = synth.sir_run(n, 3, k, dom, infected_frac=0.05)
+        x, y, z, st = synth.sir_run(n, 3, k, dom, infected_frac=frac)
         if n == 1:
             st[:] = 1
         out.append((p, dict(x=x, y=y, z=z, sir_state=st)))
@@ -56,7 +57,8 @@ def test_batch_matches_single_handles_and_history():
 
 
 def test_batch_matches_oracle():
-    runs = uneven_runs()[:3]
+    all_runs = uneven_runs()
+    runs = [all_runs[k] for k in (0, 1, 2, 6)]  # sparse, single agent, 3 boxes, dense infection
     batch = bdm.Batch([p for p, _ in runs])
     refs = []
     for k, (p, inp) in enumerate(runs):

@@ -46,3 +46,48 @@ def test_sir_graph_replay_and_large_step_size():
     got, want = sim.get_state(), ref.get_state()
     for f in ("x", "y", "z", "sir_state", "sir_counts"):
         assert np.array_equal(got[f], want[f]), f
+
+
+def compare_all(sim, ref, tag):
+    got, want = sim.get_state(), ref.get_state()
+    for f in ("x", "y", "z", "sir_state", "neighbour_count", "box_id", "sir_counts"):
+        assert np.array_equal(got[f], want[f]), (tag, f)
+
+
+def test_sir_dense_infection_matches_oracle():
+    """Most agents infected at a density of several agents per box: almost every agent pushes
+    into its neighbours' counts, many of them into the same counters."""
+    params = sir_params(120.0, 10, p_inf=0.5, p_rec=0.05)
+    x, y, z, st = synth.sir_run(4000, 9, 0, 120.0, infected_frac=0.7)
+    sim = bdm.Sim(params)
+    ref = oracle.OracleSim(params)
+    for s in (sim, ref):
+        s.add_agents(x, y, z, sir_state=st)
+    for k in range(12):
+        sim.step(1)
+        ref.step(1)
+        compare_all(sim, ref, k)
+    assert ref.get_state()["neighbour_count"].max() >= 3
+
+
+def test_sir_agents_added_between_steps_and_after_reset():
+    """Agents appended after steps join the grid index with the next ids; a reset empties the
+    handle, and a new population then runs as on a fresh handle."""
+    params = dict(sir_params(200.0, 8), capacity=3000)
+    x, y, z, st = synth.sir_run(3000, 11, 0, 200.0, infected_frac=0.05)
+    sim = bdm.Sim(params)
+    ref = oracle.OracleSim(params)
+    for s in (sim, ref):
+        s.add_agents(x[:2000], y[:2000], z[:2000], sir_state=st[:2000])
+        s.step(5)
+        s.add_agents(x[2000:], y[2000:], z[2000:], sir_state=st[2000:])
+        s.step(5)
+    compare_all(sim, ref, "appended")
+    sim.reset()
+    ref = oracle.OracleSim(params)
+    x2, y2, z2, st2 = synth.sir_run(1500, 12, 0, 200.0, infected_frac=0.1)
+    for s in (sim, ref):
+        s.add_agents(x2, y2, z2, sir_state=st2)
+        s.step(4)
+    compare_all(sim, ref, "after reset")
+
