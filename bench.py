@@ -300,7 +300,10 @@ def run_ours(args):
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
 
     sim.close()
-    ensemble = serving = None
+    ensemble = serving = plain = spheroid = None
+    if rank == 0 and not args.no_small:
+        plain = bench_plain()
+        spheroid = bench_spheroid()
     if rank == 0 and not args.no_ensemble:
         ensemble = bench_ensemble(args.ensemble_steps, args.ensemble_baseline_runs)
     if rank == 0 and args.serve_requests > 0:
@@ -329,7 +332,7 @@ def run_ours(args):
                               "frac": step_achieved / peak, "mechanics_ms_per_step": mech_ms},
             "kernels_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
-            "ensemble": ensemble, "serving": serving,
+            "plain": plain, "spheroid": spheroid, "ensemble": ensemble, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -378,6 +381,74 @@ def bench_ensemble(steps, baseline_runs):
             "one_at_a_time_agent_steps_per_s": agents * steps / t_single,
             "speedup_vs_one_at_a_time": t_single / t_batch,
             "one_at_a_time_sample_runs": baseline_runs}
+
+
+def _event_time_ms(stream, fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def bench_plain(steps=10, reps=50):
+    """Plain mechanics (4096 spheres in a 160 um cube): the FP64 check path and the mixed path,
+    `steps`-step graph replays after one untimed replay."""
+    from paper_2006_06775_gb300 import bdm
+    params, inp = synth.plain_mechanics()
+    out = {"workload": "plain mechanics: 4096 spheres, 160 um cube, d~U[8,12] um",
+           "steps_per_replay": steps, "replays": reps}
+    for prec in ("fp64", "mixed"):
+        sim = bdm.Sim(dict(params, precision=prec))
+        sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+        sim.step(steps)
+
+        def run():
+            for _ in range(reps):
+                sim.step(steps)
+        ms = _event_time_ms(sim.stream, run)
+        sim.close()
+        out[prec] = {"agent_steps_per_s": 4096 * steps * reps / (ms * 1e-3),
+                     "ms_per_step": ms / (steps * reps)}
+    return out
+
+
+def bench_spheroid(max_agents=1_000_000, max_steps=160):
+    """Tumour spheroid: 512 cells growing and dividing to about 10^6, each secreting into a 128^3
+    grid co-stepped by FTCS.  The agent count of every step is recorded in an untimed run; the same
+    seeded run is then timed step by step (one graph replay per step) after one warm-up step."""
+    from paper_2006_06775_gb300 import bdm
+    params, inp = synth.spheroid()
+    params = dict(params, capacity=1 << 21)
+    counts = []
+    sim = bdm.Sim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    while len(counts) < max_steps:
+        sim.step(1)
+        counts.append(int(sim.get_state(fields=())["n"]))
+        if counts[-1] >= max_agents:
+            break
+    sim.close()
+    sim = bdm.Sim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    sim.step(1)
+
+    def run():
+        for _ in range(len(counts) - 1):
+            sim.step(1)
+    ms = _event_time_ms(sim.stream, run)
+    n_end = int(sim.get_state(fields=())["n"])
+    sim.close()
+    assert n_end == counts[-1], (n_end, counts[-1])
+    agent_steps = float(sum(counts[1:]))
+    return {"workload": "tumour spheroid: 512 cells, growth 100 um^3/step, division at 14 um, "
+                        "secretion into a 128^3 FTCS grid",
+            "steps": len(counts) - 1, "agents_after_first_step": counts[0],
+            "agents_final": counts[-1], "agent_steps": agent_steps,
+            "agent_steps_per_s": agent_steps / (ms * 1e-3), "ms_per_step": ms / (len(counts) - 1)}
 
 
 def bench_serving(count):
@@ -447,6 +518,8 @@ def main():
                     help="re-measure the tunable knobs on this workload and cache the choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the plain-mechanics and tumour-spheroid sub-benchmarks")
     ap.add_argument("--ensemble-steps", type=int, default=1000)
     ap.add_argument("--ensemble-baseline-runs", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=300)

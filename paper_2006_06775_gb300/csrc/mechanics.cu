@@ -2,6 +2,8 @@
 // (BioDynaMo, arXiv 2006.06775, Sec. "Simulation concepts": agent operations "calculate mechanical
 // forces" and behaviours such as growth, division and secretion; force law and update: readings
 // R1-R4, sum order R6, growth/division R7, secretion R8).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace bdm {
@@ -90,17 +92,24 @@ __global__ void __launch_bounds__(kBlock, 1) k_force_fp64(
 // The nine row segments (dz, dy in {-1,0,1}) of its 27-box neighbourhood are contiguous runs of the
 // canonical order; each run is split by two box boundaries into its x-1, x, x+1 boxes (which give
 // the x shift of a candidate's box-relative offset).  Per candidate: FP32 d^2, the neighbour count,
-// a contact test; contacts are queued in four registers and flushed through the force law in order,
-// so the rare force evaluations (~9% of candidates) do not run masked in every iteration of the
-// candidate loop.  Contacts are summed in the canonical (box, id) order.  Loads go through L1:
-// consecutive agents share almost all of their neighbourhood.
+// a contact test; every candidate is written branch-free into slot nc of a shared-memory contact
+// list and nc advances only on a contact, so the force law runs only for real contacts and never
+// masked inside the candidate loop.  A full list is flushed through the force law in order; in a
+// dense row run (more than kDenseBox agents per box somewhere in the warp) every active lane flushes
+// as soon as one lane's list is full, so the force evaluations of the warp run side by side.
+// Contacts are summed in the canonical (box, id) order.  Loads go through L1: consecutive agents
+// share almost all of their neighbourhood.
 //
 // Neighbour predicate d^2 < R^2: FP32 outside a +-2^-12 relative band, the oracle's FP64 expression
-// inside it, so counts stay exact.  The agent meets itself once (d^2 = 0): counted, then removed.
-// The displacement is added to the FP64 centre (exact conversion, one FP64 add per axis).
+// inside it, so counts stay exact.  Band candidates are queued (kBQ per thread) and decided in FP64
+// after the loop; if more turn up, a second pass recounts every candidate from one d^2.  The agent
+// meets itself once (d^2 = 0): counted, then removed.  The displacement is added to the FP64 centre
+// (exact conversion, one FP64 add per axis).
 // ---------------------------------------------------------------------------------------------
 constexpr int kFT = 256;   // threads per CTA
 constexpr int kCL = 8;     // contact list length per thread
+constexpr int kBQ = 8;     // band queue length per thread
+constexpr unsigned kDenseBox = 8;  // agents per box above which a row run is treated as dense
 
 __device__ __forceinline__ void contact_force(float& Fx, float& Fy, float& Fz, float ex, float ey,
                                               float ez, float ri, float rj, float kf, float gf) {
@@ -126,18 +135,22 @@ __device__ __forceinline__ unsigned fp64_within(unsigned i, unsigned j, const do
   return e2 < R2 ? 1u : 0u;
 }
 
-// Neighbours among the band candidates (FP32 d^2 within 2^-12 of R^2), decided by the oracle's FP64
-// expression.  Up to two were queued; more (vanishingly rare) are found again by a rescan.
-__device__ __forceinline__ unsigned exact_band_count(
-    unsigned i, unsigned nband, unsigned nb0, unsigned nb1, const double* __restrict__ sx,
-    const double* __restrict__ sy, const double* __restrict__ sz, const float4* __restrict__ p4,
-    const unsigned* __restrict__ start, int ix, int iy, int iz, int d0, int d1, int d2, float4 pi,
-    float Lf, float R2lo, float R2hi, double R2) {
-  if (nband <= 2) {
-    unsigned k = fp64_within(i, nb0, sx, sy, sz, R2);
-    if (nband == 2) k += fp64_within(i, nb1, sx, sy, sz, R2);
-    return k;
-  }
+// FP64 decision of one band candidate, as a real call: a conditional call inside a loop cannot be
+// if-converted, so the loop never occupies GB300's slow FP64 pipe for candidates outside the band.
+__device__ __noinline__ unsigned fp64_within_call(unsigned i, unsigned j, const double* __restrict__ sx,
+                                                  const double* __restrict__ sy,
+                                                  const double* __restrict__ sz, double R2) {
+  return fp64_within(i, j, sx, sy, sz, R2);
+}
+
+// Neighbour count of agent i from a second pass over its 27 boxes: FP32 below the band, the oracle's
+// FP64 expression inside it.  Used when more band candidates turned up than the per-thread queue
+// holds; it replaces the first pass's count, so every candidate is decided by one d^2.
+__device__ __noinline__ unsigned band_rescan(
+    unsigned i, const double* __restrict__ sx, const double* __restrict__ sy,
+    const double* __restrict__ sz, const float4* __restrict__ p4, const unsigned* __restrict__ start,
+    int ix, int iy, int iz, int d0, int d1, int d2, float4 pi, float Lf, float R2lo, float R2hi,
+    double R2) {
   unsigned k = 0;
   const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
   for (int sg = 0; sg < 9; ++sg) {
@@ -152,19 +165,21 @@ __device__ __forceinline__ unsigned exact_band_count(
       const float px = pi.x - (j < m1 ? -Lf : (j < m2 ? 0.f : Lf));
       const float ex = px - q.x, ey = py - q.y, ez = pz - q.z;
       const float dd = ex * ex + ey * ey + ez * ez;
-      if (dd >= R2lo && dd <= R2hi) k += fp64_within(i, j, sx, sy, sz, R2);
+      if (dd < R2lo) ++k;
+      else if (dd <= R2hi) k += fp64_within_call(i, j, sx, sy, sz, R2);
     }
   }
   return k;
 }
 
-__global__ void __launch_bounds__(kFT) k_force_mixed(
+__global__ void __launch_bounds__(kFT, 3) k_force_mixed(
     const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
     const float4* __restrict__ p4, const unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, double* __restrict__ ox, double* __restrict__ oy,
     double* __restrict__ oz, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
   __shared__ unsigned s_cj[kCL][kFT];       // contact list: candidate index
   __shared__ unsigned char s_cc[kCL][kFT];  // contact list: row segment * 3 + box x
+  __shared__ unsigned s_bq[kBQ][kFT];       // band queue: candidates decided in FP64 after the loop
   const unsigned n = g->nbox ? g->n : 0u;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const double R2 = g->R2;
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(kFT) k_force_mixed(
     int nc = 0;
     // candidates with d^2 within 2^-12 of R^2 (decided in FP64 after the loop, so the FP64 code
     // never runs predicated inside it)
-    unsigned nb0 = 0, nb1 = 0, nband = 0;
+    unsigned nband = 0;
     const int t = threadIdx.x;
     auto flush = [&]() {  // force law over the listed contacts, in order
       for (int k = 0; k < nc; ++k) {
@@ -209,29 +224,41 @@ __global__ void __launch_bounds__(kFT) k_force_mixed(
       const unsigned m2 = __ldg(start + row + ix + 1);           // end of box x
       const unsigned e = __ldg(start + row + xh + 1);            // end of the run
       const float py = pi.y - (float)(sg % 3 - 1) * Lf, pz = pi.z - (float)(sg / 3 - 1) * Lf;
-      for (unsigned j = a; j < e; ++j) {
-        const float4 q = __ldg(p4 + j);
-        const unsigned bx = j < m1 ? 0u : (j < m2 ? 1u : 2u);
-        const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
-        const float ey = py - q.y;
-        const float ez = pz - q.z;
-        const float dd = ex * ex + ey * ey + ez * ez;
-        cnt += dd < R2lo ? 1u : 0u;
-        if (dd >= R2lo && dd <= R2hi) {  // near R: queue for the FP64 decision after the loop
-          nb1 = nb0;
-          nb0 = j;
-          ++nband;
+      auto run = [&](auto dense) {
+        for (unsigned j = a; j < e; ++j) {
+          const float4 q = __ldg(p4 + j);
+          const unsigned bx = j < m1 ? 0u : (j < m2 ? 1u : 2u);
+          const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
+          const float ey = py - q.y;
+          const float ez = pz - q.z;
+          const float dd = ex * ex + ey * ey + ez * ez;
+          cnt += dd < R2lo ? 1u : 0u;
+          if (dd >= R2lo && dd <= R2hi) {  // near R: queue for the FP64 decision after the loop
+            if (nband < (unsigned)kBQ) s_bq[nband][t] = j;
+            ++nband;
+          }
+          const float rs = pi.w + q.w;
+          s_cj[nc][t] = j;  // kept only if this is a contact
+          s_cc[nc][t] = (unsigned char)(sg * 3 + (int)bx);
+          nc += (dd < rs * rs && dd > 0.f) ? 1 : 0;
+          if constexpr (decltype(dense)::value) {
+            // dense rows: a full list is flushed by every active lane at once, so the lanes'
+            // force evaluations run side by side instead of one lane at a time
+            if (__any_sync(__activemask(), nc == kCL)) flush();
+          } else {
+            if (nc == kCL) flush();
+          }
         }
-        const float rs = pi.w + q.w;
-        s_cj[nc][t] = j;  // kept only if this is a contact
-        s_cc[nc][t] = (unsigned char)(sg * 3 + (int)bx);
-        nc += (dd < rs * rs && dd > 0.f) ? 1 : 0;
-        if (nc == kCL) flush();
-      }
+      };
+      if (__any_sync(__activemask(), e - a > 3u * kDenseBox)) run(std::true_type{});
+      else run(std::false_type{});
     }
     flush();
-    if (nband) cnt += exact_band_count(i, nband, nb0, nb1, sx, sy, sz, p4, start, ix, iy, iz, d0, d1,
-                                       d2, pi, Lf, R2lo, R2hi, R2);
+    if (nband > (unsigned)kBQ) {
+      cnt = band_rescan(i, sx, sy, sz, p4, start, ix, iy, iz, d0, d1, d2, pi, Lf, R2lo, R2hi, R2);
+    } else {
+      for (unsigned k = 0; k < nband; ++k) cnt += fp64_within(i, s_bq[k][t], sx, sy, sz, R2);
+    }
     cnt -= 1u;  // the agent itself
     float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
     const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
@@ -424,9 +451,10 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed_pairs(
     unsigned cnt = s_cnt[w][lane] - 1u;
     const unsigned nb = s_nb[w];
     if (nb > (unsigned)kBandCap) {
-      // band list overflowed (very rare): every agent of the warp recounts its band exactly
-      if (valid) cnt += exact_band_count(i, 3u, 0u, 0u, sx, sy, sz, p4, start, ix, iy, iz, d0, d1, d2,
-                                         pi, Lf, R2lo, R2hi, R2);
+      // band list overflowed (very rare): every agent of the warp recounts its neighbours, deciding
+      // every candidate from one d^2
+      if (valid) cnt = band_rescan(i, sx, sy, sz, p4, start, ix, iy, iz, d0, d1, d2,
+                                   pi, Lf, R2lo, R2hi, R2) - 1u;
     } else {
       for (unsigned e = 0; e < nb; ++e)
         if (s_bo[w][e] == (unsigned char)lane) cnt += fp64_within(i, s_bj[w][e], sx, sy, sz, R2);

@@ -183,6 +183,66 @@ def test_mixed_teacher_forced_integer_state_exact():
     assert worst < 2e-5, worst
 
 
+def test_dense_spheroid_teacher_forced():
+    """A densely packed state (the tumour spheroid after 52 steps of growth and division: tens of
+    agents per box, hundreds of neighbours and contacts per agent): from the same state, mixed
+    mechanics steps reproduce grid assignment and neighbour counts exactly.  Exercises the
+    collective contact flush of dense rows and the band queue under heavy load."""
+    params, inp = synth.spheroid()
+    grow = bdm.Sim(dict(params, capacity=1 << 17, diffusion_enabled=0))
+    grow.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    grow.step(52)
+    s = grow.get_state()
+    assert s["n"] >= 32768
+    mech = dict(params, growth_enabled=0, diffusion_enabled=0)
+    x, y, z, d = s["x"], s["y"], s["z"], s["diameter"]
+    sim = bdm.Sim(mech)
+    worst = 0.0
+    for k in range(3):
+        sim.reset()
+        sim.add_agents(x, y, z, d)
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle.mech_step(x, y, z, d, mech["dt"], mech["repulsion"], mech["attraction"],
+                                mech["max_displacement"], mech["interaction_radius"])
+        assert np.array_equal(got["box_id"], want["box_id"]), k
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        worst = max(worst, max(float(np.max(np.abs(got[a] - want[a]))) for a in ("x", "y", "z")))
+        x, y, z = want["x"], want["y"], want["z"]
+    assert want["neighbour_count"].mean() > 100
+    assert worst < 2e-4, worst
+
+
+def test_band_queue_overflow_is_recounted_exactly():
+    """An agent with 40 others at distance R (1 +- 2e-8): all fall in the FP32 band around R^2, more
+    than the per-thread band queue holds, so its count comes from the exact second pass; the FP64
+    decisions must split the shell exactly as the oracle does."""
+    R = 12.0
+    g = np.random.default_rng(5)
+    m = 40
+    k = np.arange(m) + 0.5
+    theta = np.arccos(1 - 2 * k / m)
+    phi = np.pi * (1 + 5 ** 0.5) * k
+    dirs = np.stack([np.cos(phi) * np.sin(theta), np.sin(phi) * np.sin(theta), np.cos(theta)], 1)
+    sign = np.where(np.arange(m) % 2 == 0, 1.0, -1.0)
+    centre = np.array([300.0, 300.0, 300.0]) + g.uniform(0, 1, 3)
+    pts = centre + dirs * (R * (1 + sign * 2e-8))[:, None]
+    x = np.concatenate([[centre[0]], pts[:, 0]])
+    y = np.concatenate([[centre[1]], pts[:, 1]])
+    z = np.concatenate([[centre[2]], pts[:, 2]])
+    d = np.full(m + 1, 6.0, np.float32)
+    params = dict(synth.MECH_DEFAULTS, precision="mixed", interaction_radius=R)
+    sim = bdm.Sim(params)
+    sim.add_agents(x, y, z, d)
+    sim.step(1)
+    got = sim.get_state()
+    want = oracle.mech_step(x, y, z, d, params["dt"], params["repulsion"], params["attraction"],
+                            params["max_displacement"], R)
+    assert want["neighbour_count"][0] == m // 2
+    assert np.array_equal(got["neighbour_count"], want["neighbour_count"])
+    assert np.array_equal(got["box_id"], want["box_id"])
+
+
 def test_mixed_ten_step_deviation_from_fp64():
     """End to end, mixed vs FP64 oracle after 10 steps (stated, and bounded)."""
     params, inp = synth.large_mechanics(n=50_000, seed=13, with_grid=False)
