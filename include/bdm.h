@@ -16,12 +16,13 @@
  *    every buffer it passes. Input pointers in this header are HOST pointers, copied in before the
  *    call returns; output pointers are HOST pointers filled before the call returns.
  *  - Ordering: state crosses the boundary in agent-id order (ids 0..n-1 in insertion order, then
- *    division daughters). Internally agents live in box order on the device.
- *  - Streams: work is enqueued on bdm_params.stream (a cudaStream_t, NULL = the legacy default
- *    stream) and is asynchronous, except bdm_get_state, which synchronises that stream. A device
- *    error word (grid overflow, capacity overflow, a bounded wait that timed out) is checked at the
- *    next synchronising call and returned as BDM_ESTATE / BDM_ENOMEM / BDM_ETIMEOUT; the handle
- *    then refuses further steps.
+ *    division daughters). Internally, mechanics agents live in box order on the device; SIR
+ *    agents stay in id order with a box-order index.
+ *  - Streams: work is enqueued on bdm_params.stream (a cudaStream_t; NULL = a non-blocking stream
+ *    the handle creates and destroys) and is asynchronous, except bdm_get_state, which
+ *    synchronises that stream. A device error word (grid overflow, capacity overflow, a bounded
+ *    wait that timed out) is checked at the next synchronising call and returned as BDM_ESTATE /
+ *    BDM_ENOMEM / BDM_ETIMEOUT; the handle then refuses further steps.
  *  - Memory: if alloc/free are given, every device allocation goes through them (for example the
  *    PyTorch caching allocator); otherwise cudaMalloc/cudaFree. All buffers are sized at creation
  *    (capacity, box_capacity); no step allocates.
@@ -99,7 +100,7 @@ typedef struct bdm_params {
                                     bdm_add_agents call                                           */
   uint64_t box_capacity;         /* max grid boxes; 0 = automatic (4 x initial + margin)           */
   /* Device plumbing. */
-  void* stream;                  /* cudaStream_t                                                   */
+  void* stream;                  /* cudaStream_t, NULL = a stream the handle creates              */
   void* (*alloc)(size_t bytes, void* user); /* optional device allocator                         */
   void (*free)(void* ptr, void* user);
   void* alloc_user;
