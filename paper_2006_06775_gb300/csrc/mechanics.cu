@@ -91,14 +91,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_force_fp64(
 // Force + capped update, mixed precision.  One thread per agent in canonical order (grid-stride).
 // The nine row segments (dz, dy in {-1,0,1}) of its 27-box neighbourhood are contiguous runs of the
 // canonical order; each run is split by two box boundaries into its x-1, x, x+1 boxes (which give
-// the x shift of a candidate's box-relative offset).  Per candidate: FP32 d^2, the neighbour count,
-// a contact test; every candidate is written branch-free into slot nc of a shared-memory contact
-// list and nc advances only on a contact, so the force law runs only for real contacts and never
-// masked inside the candidate loop.  A full list is flushed through the force law in order; in a
-// dense row run (more than kDenseBox agents per box somewhere in the warp) every active lane flushes
-// as soon as one lane's list is full, so the force evaluations of the warp run side by side.
-// Contacts are summed in the canonical (box, id) order.  Loads go through L1: consecutive agents
-// share almost all of their neighbourhood.
+// the x shift of a candidate's box-relative offset).  Per candidate the loop only evaluates FP32
+// d^2 and writes the candidate branch-free into slot nc of a shared-memory list, advancing nc when
+// d^2 <= R^2 (1 + 2^-12): every neighbour, band candidate and contact is listed (about 5 of 26
+// candidates at 0.3 volume fraction).  A flush then takes the listed candidates in order: the
+// neighbour count, the band queue and, for contacts, the force law, so none of that runs masked in
+// every iteration of the candidate loop.  In a dense row run (more than kDenseBox agents per box
+// somewhere in the warp) every active lane flushes as soon as one lane's list is full, so the
+// flushes of the warp run side by side.  Contacts are summed in the canonical (box, id) order.
+// Loads go through L1: consecutive agents share almost all of their neighbourhood.
 //
 // Neighbour predicate d^2 < R^2: FP32 outside a +-2^-12 relative band, the oracle's FP64 expression
 // inside it, so counts stay exact.  Band candidates are queued (kBQ per thread) and decided in FP64
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_force_fp64(
 // (exact conversion, one FP64 add per axis).
 // ---------------------------------------------------------------------------------------------
 constexpr int kFT = 256;   // threads per CTA
-constexpr int kCL = 8;     // contact list length per thread
+constexpr int kCL = 16;    // candidate list length per thread
 constexpr int kBQ = 8;     // band queue length per thread
 constexpr unsigned kDenseBox = 8;  // agents per box above which a row run is treated as dense
 
@@ -177,8 +178,8 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
     const float4* __restrict__ p4, const unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, double* __restrict__ ox, double* __restrict__ oy,
     double* __restrict__ oz, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
-  __shared__ unsigned s_cj[kCL][kFT];       // contact list: candidate index
-  __shared__ unsigned char s_cc[kCL][kFT];  // contact list: row segment * 3 + box x
+  __shared__ unsigned s_cj[kCL][kFT];       // candidate list: index
+  __shared__ unsigned char s_cc[kCL][kFT];  // candidate list: row segment * 3 + box x
   __shared__ unsigned s_bq[kBQ][kFT];       // band queue: candidates decided in FP64 after the loop
   const unsigned n = g->nbox ? g->n : 0u;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
@@ -199,10 +200,10 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     int nc = 0;
     // candidates with d^2 within 2^-12 of R^2 (decided in FP64 after the loop, so the FP64 code
-    // never runs predicated inside it)
+    // never runs predicated inside the candidate loop)
     unsigned nband = 0;
     const int t = threadIdx.x;
-    auto flush = [&]() {  // force law over the listed contacts, in order
+    auto flush = [&]() {  // count, band queue and force law over the listed candidates, in order
       for (int k = 0; k < nc; ++k) {
         const unsigned cj = s_cj[k][t], cc = s_cc[k][t];
         const float4 q = __ldg(p4 + cj);
@@ -210,7 +211,15 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
         const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q.x;
         const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
         const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
-        contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q.w, c.kf, c.gammaf);
+        const float dd = ex * ex + ey * ey + ez * ez;
+        if (dd < R2lo) {
+          ++cnt;
+        } else {  // near R: queued for the FP64 decision after the loop
+          if (nband < (unsigned)kBQ) s_bq[nband][t] = cj;
+          ++nband;
+        }
+        const float rs = pi.w + q.w;
+        if (dd < rs * rs && dd > 0.f) contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q.w, c.kf, c.gammaf);
       }
       nc = 0;
     };
@@ -232,15 +241,9 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
           const float ey = py - q.y;
           const float ez = pz - q.z;
           const float dd = ex * ex + ey * ey + ez * ez;
-          cnt += dd < R2lo ? 1u : 0u;
-          if (dd >= R2lo && dd <= R2hi) {  // near R: queue for the FP64 decision after the loop
-            if (nband < (unsigned)kBQ) s_bq[nband][t] = j;
-            ++nband;
-          }
-          const float rs = pi.w + q.w;
-          s_cj[nc][t] = j;  // kept only if this is a contact
+          s_cj[nc][t] = j;  // kept only if within R (every neighbour, band candidate and contact)
           s_cc[nc][t] = (unsigned char)(sg * 3 + (int)bx);
-          nc += (dd < rs * rs && dd > 0.f) ? 1 : 0;
+          nc += dd <= R2hi ? 1 : 0;
           if constexpr (decltype(dense)::value) {
             // dense rows: a full list is flushed by every active lane at once, so the lanes'
             // force evaluations run side by side instead of one lane at a time
