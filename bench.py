@@ -295,6 +295,15 @@ def run_ours(args):
                         "frac": achieved_gb / peak, "peak_kind": peak_kind,
                         "alg_bytes_per_agent": KERNEL_BYTES["force_mixed"](boxes_per_agent)}}
 
+    diffusion = None
+    if "ftcs" in per_launch:
+        vox = 512 ** 3
+        dms = per_launch["ftcs"]
+        diffusion = {"grid": "512^3 FP32, FTCS + FP64 mass, co-stepped", "ms_per_step": dms,
+                     "voxel_steps_per_s": vox / (dms * 1e-3), "alg_bytes_per_voxel": 8,
+                     "achieved": 8 * vox / (dms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": 8 * vox / (dms * 1e-3) / 1e9 / peak}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
@@ -329,8 +338,11 @@ def run_ours(args):
             "step_roofline": {"bytes_per_agent_step": STEP_BYTES_PER_AGENT(boxes_per_agent),
                               "diffusion_bytes_per_step": 8 * 512 ** 3,
                               "achieved": step_achieved, "peak": peak, "unit": "GB/s",
-                              "frac": step_achieved / peak, "mechanics_ms_per_step": mech_ms},
+                              "frac": step_achieved / peak, "nominal_peak": 7900.0,
+                              "frac_of_nominal": step_achieved / 7900.0,
+                              "mechanics_ms_per_step": mech_ms},
             "kernels_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
+            "diffusion": diffusion,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plain": plain, "spheroid": spheroid, "ensemble": ensemble, "serving": serving,
         }
@@ -432,23 +444,41 @@ def bench_spheroid(max_agents=1_000_000, max_steps=160):
         if counts[-1] >= max_agents:
             break
     sim.close()
+    import torch
     sim = bdm.Sim(params)
     sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
     sim.step(1)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(len(counts))]
 
     def run():
-        for _ in range(len(counts) - 1):
+        marks[0].record(sim.stream)
+        for k in range(1, len(counts)):
             sim.step(1)
+            marks[k].record(sim.stream)
     ms = _event_time_ms(sim.stream, run)
-    n_end = int(sim.get_state(fields=())["n"])
+    st = sim.get_state(fields=())
     sim.close()
-    assert n_end == counts[-1], (n_end, counts[-1])
+    assert int(st["n"]) == counts[-1], (st["n"], counts[-1])
+    step_ms = [marks[k - 1].elapsed_time(marks[k]) for k in range(1, len(counts))]
+    by_n = {}
+    for k in range(1, len(counts)):
+        by_n.setdefault(counts[k], []).append(step_ms[k - 1])
+    # closed-form mass: secretion q per agent, then decay (zero-flux walls conserve the rest)
+    keep = 1.0 - params["decay"] * params["dt_diffusion"]
+    mass = 0.0
+    for n in counts:
+        mass = keep * (mass + params["secretion"] * n)
     agent_steps = float(sum(counts[1:]))
     return {"workload": "tumour spheroid: 512 cells, growth 100 um^3/step, division at 14 um, "
                         "secretion into a 128^3 FTCS grid",
             "steps": len(counts) - 1, "agents_after_first_step": counts[0],
             "agents_final": counts[-1], "agent_steps": agent_steps,
-            "agent_steps_per_s": agent_steps / (ms * 1e-3), "ms_per_step": ms / (len(counts) - 1)}
+            "agent_steps_per_s": agent_steps / (ms * 1e-3), "ms_per_step": ms / (len(counts) - 1),
+            "by_agents": [{"agents": n, "steps": len(v), "ms_per_step": sum(v) / len(v),
+                           "agent_steps_per_s": n * len(v) / (sum(v) * 1e-3)}
+                          for n, v in sorted(by_n.items())],
+            "mass_total": st["mass_total"], "mass_closed_form": mass,
+            "mass_rel_error": abs(st["mass_total"] - mass) / mass}
 
 
 def bench_serving(count):

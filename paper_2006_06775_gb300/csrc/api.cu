@@ -397,7 +397,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
   const size_t need = (C + kBlock - 1) / kBlock;
   s->blocks_stream = (int)std::max<size_t>(1, std::min<size_t>(need, stream_blocks));
   s->blocks_force = s->mixed ? s->sms * force_mixed_blocks_per_sm(s->mc.force_variant)
-                             : (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)s->sms * 4));
+                             : force_fp64_blocks(C, s->sms);
   const size_t tiles = s->is_sir ? s->sb.max_tiles : s->mb.max_tiles;
   s->blocks_scan = (int)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)s->sms * 4));
   s->allocated = true;

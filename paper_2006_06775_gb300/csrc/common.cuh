@@ -230,6 +230,7 @@ void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_
 void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                   MechConsts c, bool mixed, int grid_blocks);
 int force_mixed_blocks_per_sm(int variant);
+int force_fp64_blocks(size_t capacity, int sms);  // grid of the FP64 force kernel
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                  double dv, double vdiv, int grid_blocks);
 void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -16,7 +16,11 @@ namespace bdm {
 // positions can match the FP64 oracle bit for bit.  The epilogue folds the new centres into the
 // bounds of the next step's grid.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock, 1) k_force_fp64(
+// One warp per block: at the small populations this check path is used on, the agents spread over
+// as many SMs as possible (each thread is a long chain of FP64 divisions and square roots).
+constexpr int kF64 = 32;
+
+__global__ void __launch_bounds__(kF64) k_force_fp64(
     const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
     const float* __restrict__ diam, const unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, double* __restrict__ ox, double* __restrict__ oy,
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_force_fp64(
     const unsigned dbits = __float_as_uint(diam[i]);
     md = dbits > md ? dbits : md;
   }
-  block_commit_bounds(mn, mx, md, g);
+  block_commit_bounds<kF64>(mn, mx, md, g);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -489,6 +493,12 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed_pairs(
   block_commit_bounds<kFT>(mn, mx, md, g);
 }
 
+int force_fp64_blocks(size_t capacity, int sms) {
+  const size_t need = (capacity + kF64 - 1) / kF64;
+  const size_t cap = (size_t)sms * 16;
+  return (int)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
 int force_mixed_blocks_per_sm(int variant) {
   int nb = 0;
   if (variant == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed_pairs, kFT, 0);
@@ -665,7 +675,7 @@ void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr,
     k_force_mixed<<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.p4, b.skey,
                                               b.start, b.pos.x, b.pos.y, b.pos.z, b.nbr, g, c);
   else
-    k_force_fp64<<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, attr.diam,
+    k_force_fp64<<<grid_blocks, kF64, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, attr.diam,
                                                 b.skey, b.start, b.pos.x, b.pos.y, b.pos.z, b.nbr,
                                                 g, c);
 }
