@@ -65,7 +65,13 @@ typedef struct bdm_params {
   double attraction;             /* gamma                                                          */
   double max_displacement;       /* cap on |displacement| per step                                 */
   double interaction_radius;     /* neighbour radius R; 0 = largest diameter, every step          */
-  double box_length;             /* grid box L >= R; 0 = R                                         */
+  double box_length;             /* grid box L >= R + skin; 0 = R + skin                           */
+  double skin;                   /* neighbour-list skin (mixed precision without growth; 0 = off):
+                                    the grid is rebuilt and each agent's candidates within R + skin
+                                    are listed only when some agent has moved more than skin / 2
+                                    since the last rebuild (or after 64 steps); the steps between
+                                    evaluate the lists.  Integer state stays exact every step; the
+                                    FP32 force sums follow the order of the last rebuild.          */
   /* Growth and division (reading R7). */
   int32_t growth_enabled;
   int32_t force_variant;         /* mixed force kernel: 0 = one thread per agent, 1 = warp-shared
@@ -125,7 +131,7 @@ typedef struct bdm_state {
   float* grid;                   /* substance grid, x fastest                                      */
   double mass_total;             /* out: FP64 total of the substance grid                          */
   uint32_t sir_counts[3];        /* out: S, I, R after the last step                               */
-  uint32_t reserved1;
+  uint32_t grid_rebuilds;        /* out: grid rebuilds so far (mechanics; = steps without skin)    */
   int64_t grid_origin_q[3];      /* out: last grid origin, 2^-20 um lattice units (mechanics)      */
   int64_t grid_box_q;            /* out: box length, lattice units                                 */
   int64_t grid_dims[3];          /* out: boxes per axis                                            */

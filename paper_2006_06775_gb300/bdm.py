@@ -26,7 +26,7 @@ class Params(ctypes.Structure):
         ("record_diagnostics", ctypes.c_int32),
         ("dt", ctypes.c_double), ("repulsion", ctypes.c_double), ("attraction", ctypes.c_double),
         ("max_displacement", ctypes.c_double), ("interaction_radius", ctypes.c_double),
-        ("box_length", ctypes.c_double),
+        ("box_length", ctypes.c_double), ("skin", ctypes.c_double),
         ("growth_enabled", ctypes.c_int32), ("force_variant", ctypes.c_int32),
         ("growth_volume", ctypes.c_double), ("division_volume", ctypes.c_double),
         ("division_offset_frac", ctypes.c_double),
@@ -53,7 +53,7 @@ class State(ctypes.Structure):
         ("diameter", ctypes.c_void_p), ("volume", ctypes.c_void_p), ("sir_state", ctypes.c_void_p),
         ("neighbour_count", ctypes.c_void_p), ("box_id", ctypes.c_void_p), ("grid", ctypes.c_void_p),
         ("mass_total", ctypes.c_double), ("sir_counts", ctypes.c_uint32 * 3),
-        ("reserved1", ctypes.c_uint32), ("grid_origin_q", ctypes.c_int64 * 3),
+        ("grid_rebuilds", ctypes.c_uint32), ("grid_origin_q", ctypes.c_int64 * 3),
         ("grid_box_q", ctypes.c_int64), ("grid_dims", ctypes.c_int64 * 3),
     ]
 
@@ -144,7 +144,7 @@ def make_params(d: dict) -> Params:
     prec = d.get("precision", "mixed")
     p.precision = BDM_FP64 if prec in ("fp64", BDM_FP64) else BDM_MIXED
     for name in ("dt", "repulsion", "attraction", "max_displacement", "interaction_radius",
-                 "box_length", "growth_volume", "division_volume", "division_offset_frac", "voxel",
+                 "box_length", "skin", "growth_volume", "division_volume", "division_offset_frac", "voxel",
                  "diffusion_coeff", "decay", "dt_diffusion", "secretion", "sir_domain", "sir_radius",
                  "sir_step", "p_infect", "p_recover"):
         if name in d:
@@ -234,7 +234,7 @@ def bdm_get_state(h, fields=FIELDS, grid_size=0, out=None):
     _check(L.bdm_get_state(h, ctypes.byref(st2)), h)
     res = dict(arrays)
     res.update(n=int(st2.n), step=int(st2.step), mass_total=float(st2.mass_total),
-               sir_counts=np.array(st2.sir_counts[:], np.uint32),
+               sir_counts=np.array(st2.sir_counts[:], np.uint32), grid_rebuilds=int(st2.grid_rebuilds),
                grid_origin_q=np.array(st2.grid_origin_q[:], np.int64),
                grid_box_q=int(st2.grid_box_q), grid_dims=np.array(st2.grid_dims[:], np.int64))
     return res

@@ -217,8 +217,12 @@ int check_params(bdm_sim* s, const bdm_params* p) {
       return fail(s, BDM_EINVAL, "interaction_radius/box_length must be >= 0");
     if (p->force_variant != 0 && p->force_variant != 1)
       return fail(s, BDM_EINVAL, "force_variant must be 0 or 1");
-    if (p->box_length > 0.0 && p->interaction_radius > 0.0 && p->box_length < p->interaction_radius)
-      return fail(s, BDM_EINVAL, "box_length below interaction_radius");
+    if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) return fail(s, BDM_EINVAL, "skin must be >= 0");
+    if (p->box_length > 0.0 && p->interaction_radius > 0.0 &&
+        p->box_length < p->interaction_radius + p->skin)
+      return fail(s, BDM_EINVAL, "box_length below interaction_radius + skin");
+    if (p->skin > 0.0 && (p->precision != BDM_MIXED || p->growth_enabled || p->force_variant != 0))
+      return fail(s, BDM_EINVAL, "a neighbour-list skin needs mixed precision, no growth, force_variant 0");
     if (p->growth_enabled) {
       if (!(p->growth_volume >= 0.0) || !(p->division_volume > 0.0) ||
           !(p->division_offset_frac >= 0.0))
@@ -324,7 +328,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
           R = 0.0;
           for (size_t i = 0; i < n_first; ++i) R = std::max(R, (double)d[i]);
         }
-        const double L = p.box_length > 0.0 ? p.box_length : R;
+        const double L = p.box_length > 0.0 ? p.box_length : R + p.skin;
         const double* c[3] = {x, y, z};
         for (int a = 0; a < 3; ++a) {
           double lo = c[a][0], hi = c[a][0];
@@ -354,6 +358,15 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
         (rc = dalloc_n(s, &b.start, boxcap + 1)))
       return rc;
     if (s->mixed && (rc = dalloc_n(s, &b.p4, C))) return rc;
+    if (p.skin > 0.0) {
+      if (C >= (1ull << 27)) return fail(s, BDM_EINVAL, "a neighbour-list skin supports up to 2^27 agents");
+      if ((rc = dalloc_n(s, &b.list, (size_t)kListCap * ((C + 31) / 32 * 32))) || (rc = dalloc_n(s, &b.list_n, C)) ||
+          (rc = dalloc_n(s, &b.disp, C)) || (rc = dalloc_n(s, &b.delta[0], C)) ||
+          (rc = dalloc_n(s, &b.delta[1], C)) || (rc = dalloc_n(s, &b.delta[2], C)))
+        return rc;
+      CK(cudaMemsetAsync(b.list_n, 0, sizeof(unsigned) * C, s->stream));
+      CK(cudaMemsetAsync(b.disp, 0, sizeof(float) * C, s->stream));
+    }
     b.max_tiles = scan_tiles_for(boxcap + 1);
     if ((rc = dalloc_n(s, &b.tiles[0], b.max_tiles))) return rc;
     if (s->growth) {
@@ -378,6 +391,9 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     mc.box_capacity = (unsigned)std::min<size_t>(boxcap, 0xFFFFFFF0ull);
     mc.capacity = (unsigned)C;
     mc.force_variant = p.force_variant;
+    mc.skin = p.skin;
+    mc.skin_half = (float)(0.5 * p.skin * (1.0 - 1e-5));
+    mc.max_cadence = 64;
   }
   if (s->diffusion) {
     const size_t nv = (size_t)p.grid_n[0] * p.grid_n[1] * p.grid_n[2];
@@ -396,7 +412,8 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
   const int stream_blocks = s->sms * 8;
   const size_t need = (C + kBlock - 1) / kBlock;
   s->blocks_stream = (int)std::max<size_t>(1, std::min<size_t>(need, stream_blocks));
-  s->blocks_force = s->mixed ? s->sms * force_mixed_blocks_per_sm(s->mc.force_variant)
+  s->blocks_force = s->mixed ? s->sms * (p.skin > 0.0 ? force_skin_blocks_per_sm()
+                                                      : force_mixed_blocks_per_sm(s->mc.force_variant))
                              : force_fp64_blocks(C, s->sms);
   const size_t tiles = s->is_sir ? s->sb.max_tiles : s->mb.max_tiles;
   s->blocks_scan = (int)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)s->sms * 4));
@@ -469,14 +486,25 @@ int enqueue_mech_step(bdm_sim* s) {
   }
   RUN("finalize", 1, launch_finalize(st, g, s->mc));
   CK(cudaMemsetAsync(b.tiles[0], 0, sizeof(unsigned long long) * b.max_tiles, st));
+  // with a skin, finalize decides on the device whether this step rebuilds: the rebuild kernels
+  // then see 0 agents / 0 boxes on list steps, and the two force kernels skip the other kind
   RUN("key_hist", 1, launch_key_hist(st, b, g, s->blocks_stream));
-  RUN("scan_box", 1, launch_scan(st, b.count, b.start, &g->nbox1, b.tiles[0], &g->scan_ctr[0], &g->err, 1,
-                                 s->blocks_scan));
+  RUN("scan_box", 1, launch_scan(st, b.count, b.start, &g->nbox1_sort, b.tiles[0], &g->scan_ctr[0], &g->err,
+                                 1, s->blocks_scan));
   RUN("scatter", 1, launch_scatter(st, b, g, s->blocks_stream));
   RUN("gather", 1, launch_gather(st, b, A, B, g, s->mixed, s->blocks_stream));
-  RUN(s->mixed ? "force_mixed" : "force_fp64", 1, launch_force(st, b, B, g, s->mc, s->mixed, s->blocks_force));
-  s->bounds_fresh = !s->growth;
-  s->attr_cur ^= 1;
+  if (s->mc.skin > 0.0) {
+    RUN("attr_copy", 1, launch_attr_copy(st, B, A, g, s->blocks_stream));
+    RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_stream));
+    RUN("force_walk", 1, launch_force_skin(st, b, g, s->mc, true, s->blocks_force));  // overflow only
+    RUN("force_list", 1, launch_force_skin(st, b, g, s->mc, false, s->blocks_force));
+    RUN("apply", 1, launch_apply_skin(st, b, A, g, s->mc, s->blocks_stream));
+    s->bounds_fresh = true;  // attributes stay in A
+  } else {
+    RUN(s->mixed ? "force_mixed" : "force_fp64", 1, launch_force(st, b, B, g, s->mc, s->mixed, s->blocks_force));
+    s->bounds_fresh = !s->growth;
+    s->attr_cur ^= 1;
+  }
   if (s->diffusion) {
     if (p.secretion != 0.0)
       RUN("secrete", 1, launch_secrete(st, b, g, s->grid[s->grid_cur], s->gdims, p.grid_origin, p.voxel,
@@ -671,6 +699,7 @@ int bdm_add_agents(bdm_sim* s, size_t n, const double* x, const double* y, const
     return fail(s, BDM_EINVAL, "agent %u: diameter must be > 0 and |position| < 1e9", s->gh->bad_input);
   s->n_stage = (unsigned)(n0 + n);
   CK(cudaMemcpyAsync(&s->g->n, &s->n_stage, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(&s->g->list_valid, 0, sizeof(unsigned), st));  // the next step rebuilds
   s->n_host = n0 + n;
   s->bounds_fresh = false;
   CK(cudaStreamSynchronize(st));
@@ -712,6 +741,8 @@ int bdm_reset(bdm_sim* s) {
   s->gh->err = 0;
   s->gh->sir_counts[0] = s->gh->sir_counts[1] = s->gh->sir_counts[2] = 0;
   s->gh->sir_sources = 0;
+  s->gh->list_valid = 0;
+  s->gh->rebuilds = 0;
   CK(cudaMemcpy(s->g, s->gh, sizeof(DevGrid), cudaMemcpyHostToDevice));
   // the SIR box histogram already holds the removed agents for their next step
   if (s->is_sir) CK(cudaMemset(s->sb.count, 0, sizeof(unsigned) * (s->box_capacity + 1)));
@@ -772,6 +803,7 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
     st->grid_dims[k] = G.dims[k];
   }
   st->grid_box_q = G.Lq;
+  st->grid_rebuilds = G.rebuilds;
   cudaStream_t sm = s->stream;
   if (s->is_sir) {
     const SirState& S = s->sb.a;

@@ -56,6 +56,18 @@ struct DevGrid {
   unsigned long long step;        // steps completed (Philox counters)
   unsigned bad_input;             // first rejected agent of the last upload (~0u: none)
   double mass;                    // FP64 substance total after the last diffusion step
+  // neighbour lists (mixed precision with a skin): which part of the step runs is decided here by
+  // the finalize kernel, so one captured step serves rebuild and list steps alike
+  unsigned n_sort;                // agents the grid rebuild sorts this step (n, or 0 on list steps)
+  unsigned nbox1_sort;            // items of this step's box scan (nbox + 1, or 0 on list steps)
+  unsigned rebuild;               // 1: this step rebuilds the grid and the lists
+  unsigned list_valid;            // lists describe the current agents (cleared by uploads)
+  unsigned list_overflow;         // an agent had more listed candidates than the list holds
+  unsigned max_disp;              // float bits: max over agents of |moves| since the last rebuild
+  unsigned since_rebuild;         // steps since the last rebuild
+  unsigned rebuilds;              // rebuilds so far
+  float list_L2f;                 // list radius squared (R + skin)^2, widened by 2^-10
+  float Lf_list;                  // box length (um) of the grid the lists were built on
 };
 
 struct MechConsts {               // per-simulation constants passed by value
@@ -64,6 +76,9 @@ struct MechConsts {               // per-simulation constants passed by value
   double interaction_radius, box_length;
   unsigned box_capacity, capacity;
   int force_variant;              // 0: one thread per agent, 1: warp-shared pairs
+  double skin;                    // neighbour-list skin (um); 0: grid walk every step
+  float skin_half;                // rebuild when an agent may have moved more than this
+  unsigned max_cadence;           // rebuild at least every this many steps (bounds FP32 drift)
 };
 
 // ---- exact helpers -------------------------------------------------------------------------
@@ -213,6 +228,12 @@ struct MechBuffers {
   unsigned* flag;                // growth: divide flags by id; also the division rank array
   unsigned* drank;
   unsigned max_tiles;
+  // neighbour lists (skin > 0): kListCap entries per agent, interleaved per group of 32 agents;
+  // an entry is (j << 5) | (row * 3 + box x) in the sorted order and grid of the last rebuild
+  unsigned* list;
+  unsigned* list_n;
+  float* disp;                   // |moves| of each agent since the last rebuild
+  float* delta[3];               // this step's capped displacement
 };
 
 // grid.cu
@@ -231,6 +252,17 @@ void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr,
                   MechConsts c, bool mixed, int grid_blocks);
 int force_mixed_blocks_per_sm(int variant);
 int force_fp64_blocks(size_t capacity, int sms);  // grid of the FP64 force kernel
+constexpr unsigned kListCap = 32;  // listed candidates per agent (R + skin)
+// neighbour-list steps (mechanics.cu): the walk that also lists, the list-driven force, the in-place
+// update, and the attribute copy that keeps one attribute buffer current
+void launch_force_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, MechConsts c, bool build,
+                       int grid_blocks);
+void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
+void launch_apply_skin(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                       MechConsts c, int grid_blocks);
+void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
+                      int grid_blocks);
+int force_skin_blocks_per_sm();
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                  double dv, double vdiv, int grid_blocks);
 void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

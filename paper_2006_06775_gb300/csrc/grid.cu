@@ -42,8 +42,8 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
   } else {
     double R = c.interaction_radius > 0.0 ? c.interaction_radius
                                           : (double)__uint_as_float(g->acc_maxdiam);
-    double L = c.box_length > 0.0 ? c.box_length : R;
-    bool ok = (R > 0.0) && (L >= R) && (L < 2048.0);
+    double L = c.box_length > 0.0 ? c.box_length : R + c.skin;
+    bool ok = (R > 0.0) && (L >= R + c.skin) && (L < 2048.0);
     long long Lq = (long long)ceil(L * kQScale);
     unsigned long long nbox = 1;
     long long O[3];
@@ -83,8 +83,30 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
       g->R2lo = g->R2f * (1.0f - 1.0f / 4096.0f);
       g->R2hi = g->R2f * (1.0f + 1.0f / 4096.0f);
       g->invLq = (float)(1.0 / (double)Lq);
-
+      g->list_L2f = (float)((R + c.skin) * (R + c.skin)) * (1.0f + 1.0f / 1024.0f);
     }
+  }
+  // Rebuild the grid this step, or evaluate the neighbour lists of the last rebuild (skin > 0).  A
+  // pair within R now was within R + skin at the last rebuild while no agent has moved more than
+  // skin / 2 since, so its lists still hold every neighbour and contact.
+  unsigned rebuild = 1u;
+  if (c.skin > 0.0 && g->nbox && g->list_valid && !g->list_overflow && g->Lf == g->Lf_list &&
+      __uint_as_float(g->max_disp) <= c.skin_half && g->since_rebuild + 1u < c.max_cadence)
+    rebuild = 0u;
+  g->rebuild = rebuild;
+  if (rebuild) {
+    g->n_sort = g->nbox ? n : 0u;
+    g->nbox1_sort = g->nbox1;
+    g->list_valid = c.skin > 0.0 && g->nbox ? 1u : 0u;
+    g->list_overflow = 0u;
+    g->max_disp = 0u;
+    g->since_rebuild = 0u;
+    g->Lf_list = g->Lf;
+    g->rebuilds += 1u;
+  } else {
+    g->n_sort = 0u;
+    g->nbox1_sort = 0u;
+    g->since_rebuild += 1u;
   }
   for (int a = 0; a < 3; ++a) {
     g->acc_min[a] = ~0ull;
@@ -100,7 +122,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(const double* __restrict__ 
                                                      unsigned* __restrict__ key,
                                                      unsigned* __restrict__ rank,
                                                      unsigned* __restrict__ count, DevGrid* g) {
-  const unsigned n = g->nbox ? g->n : 0u;
+  const unsigned n = g->nbox ? g->n_sort : 0u;
   const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const float inv = g->invLq;
@@ -132,7 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const unsigned* __restrict__
                                                     const unsigned* __restrict__ rank,
                                                     const unsigned* __restrict__ start,
                                                     unsigned* __restrict__ perm, DevGrid* g) {
-  const unsigned n = g->nbox ? g->n : 0u;
+  const unsigned n = g->nbox ? g->n_sort : 0u;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     perm[start[key[i]] + rank[i]] = i;
 }
@@ -147,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(
     const double* __restrict__ sy, const double* __restrict__ sz, AgentArrays src,
     double* __restrict__ dx, double* __restrict__ dy, double* __restrict__ dz, AgentArrays dst,
     unsigned* __restrict__ skey, float4* __restrict__ p4, DevGrid* g) {
-  const unsigned n = g->nbox ? g->n : 0u;
+  const unsigned n = g->nbox ? g->n_sort : 0u;
   const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
   const unsigned d0 = (unsigned)g->dims[0], d1 = (unsigned)g->dims[1];
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {

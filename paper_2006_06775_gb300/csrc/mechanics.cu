@@ -291,6 +291,329 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
 }
 
 // ---------------------------------------------------------------------------------------------
+// Neighbour-list steps (skin > 0).  A rebuild step runs the canonical 27-box walk of k_force_mixed
+// on a grid whose box length is at least R + skin, and also lists, per agent, every candidate within
+// R + skin ((j << 5) | (row * 3 + box x), in canonical order).  The steps between evaluate those
+// lists instead of walking the grid: while no agent has moved more than skin / 2, every pair
+// within R was within R + skin at the rebuild, so every neighbour and contact is listed.  Counts use
+// the same FP32 band + FP64 decision as the walk, so they stay exact; the FP32 force sums follow
+// the list (the canonical order of the last rebuild).  Both kernels write the capped displacement;
+// k_apply_skin then moves the FP64 centres and FP32 offsets in place.
+// ---------------------------------------------------------------------------------------------
+
+// List layout: the entries of the 32 agents of one warp-sized group are interleaved, entry k of agent
+// i at (i / 32) * 32 * kListCap + k * 32 + i % 32, so entry k of a warp's agents is one 128-byte
+// line and every line read is fully used.
+__device__ __forceinline__ size_t list_at(unsigned i, unsigned k) {
+  return (size_t)(i >> 5) * (32u * kListCap) + (size_t)k * 32u + (i & 31u);
+}
+
+// Neighbour count of agent i over its m listed candidates, each decided from one d^2 (used when the
+// band queue overflows).
+__device__ __noinline__ unsigned list_rescan(unsigned i, unsigned m, const unsigned* __restrict__ list,
+                                             const double* __restrict__ sx,
+                                             const double* __restrict__ sy,
+                                             const double* __restrict__ sz,
+                                             const float4* __restrict__ p4, float4 pi, float Lf,
+                                             float R2lo, float R2hi, double R2) {
+  unsigned k = 0;
+  for (unsigned e = 0; e < m; ++e) {
+    const unsigned v = list[list_at(i, e)];
+    const unsigned j = v >> 5, cc = v & 31u;
+    const float4 q = p4[j];
+    const int sgk = (int)(cc / 3u), bxk = (int)(cc % 3u);
+    const float ex = (pi.x - (float)(bxk - 1) * Lf) - q.x;
+    const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
+    const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
+    const float dd = ex * ex + ey * ey + ez * ez;
+    if (dd < R2lo) ++k;
+    else if (dd <= R2hi) k += fp64_within_call(i, j, sx, sy, sz, R2);
+  }
+  return k;
+}
+
+template <bool BUILD>
+__global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
+    const double* __restrict__ gx, const double* __restrict__ gy, const double* __restrict__ gz,
+    const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pz,
+    const float4* __restrict__ p4, const unsigned* __restrict__ skey,
+    const unsigned* __restrict__ start, unsigned* __restrict__ list, unsigned* __restrict__ list_n,
+    float* __restrict__ ddx, float* __restrict__ ddy, float* __restrict__ ddz,
+    unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
+  // BUILD: the walk with forces, only on a rebuild step whose lists overflowed; otherwise the lists
+  // (built by k_list_build on a rebuild step) give the forces
+  if (BUILD ? !(g->rebuild && g->list_overflow) : g->list_overflow != 0u) return;
+  __shared__ unsigned s_cj[kCL][kFT];       // candidate list: index
+  __shared__ unsigned char s_cc[kCL][kFT];  // candidate list: row segment * 3 + box x
+  __shared__ unsigned s_bq[kBQ][kFT];       // band queue: candidates decided in FP64 after the loop
+  const unsigned n = g->nbox ? g->n : 0u;
+  const bool rb = g->rebuild != 0u;
+  // step-start centres: gathered on a rebuild step, in place otherwise
+  const double* __restrict__ sx = rb ? gx : px;
+  const double* __restrict__ sy = rb ? gy : py;
+  const double* __restrict__ sz = rb ? gz : pz;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const double R2 = g->R2;
+  const float Lf = BUILD ? g->Lf : g->Lf_list, R2lo = g->R2lo, R2hi = g->R2hi, L2 = g->list_L2f;
+  const int t = threadIdx.x;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 pi = __ldg(p4 + i);
+    const float pxm = pi.x + Lf, px0 = pi.x, pxp = pi.x - Lf;  // neighbour box at x-1, x, x+1
+    unsigned cnt = 0;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    int nc = 0;
+    unsigned nband = 0;
+    auto flush = [&]() {  // count, band queue and force law over the staged candidates, in order
+      for (int k = 0; k < nc; ++k) {
+        const unsigned cj = s_cj[k][t], cc = s_cc[k][t];
+        const float4 q = __ldg(p4 + cj);
+        const int sgk = (int)(cc / 3u), bxk = (int)(cc % 3u);
+        const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q.x;
+        const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
+        const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
+        const float dd = ex * ex + ey * ey + ez * ez;
+        if (dd < R2lo) {
+          ++cnt;
+        } else {  // near R: queued for the FP64 decision after the loop
+          if (nband < (unsigned)kBQ) s_bq[nband][t] = cj;
+          ++nband;
+        }
+        const float rs = pi.w + q.w;
+        if (dd < rs * rs && dd > 0.f) contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q.w, c.kf, c.gammaf);
+      }
+      nc = 0;
+    };
+    if constexpr (BUILD) {
+      const unsigned b = __ldg(skey + i);
+      const int ix = (int)(b % (unsigned)d0);
+      const unsigned q0 = b / (unsigned)d0;
+      const int iy = (int)(q0 % (unsigned)d1), iz = (int)(q0 / (unsigned)d1);
+      const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
+      unsigned ln = 0;
+#pragma unroll 1
+      for (int sg = 0; sg < 9; ++sg) {
+        const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
+        if (jz < 0 || jz >= d2 || jy < 0 || jy >= d1) continue;
+        const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
+        const unsigned a = __ldg(start + row + xl);
+        const unsigned m1 = ix > 0 ? __ldg(start + row + ix) : a;  // end of box x-1
+        const unsigned m2 = __ldg(start + row + ix + 1);           // end of box x
+        const unsigned e = __ldg(start + row + xh + 1);            // end of the run
+        const float py = pi.y - (float)(sg % 3 - 1) * Lf, pz = pi.z - (float)(sg / 3 - 1) * Lf;
+        auto run = [&](auto dense) {
+          for (unsigned j = a; j < e; ++j) {
+            const float4 q = __ldg(p4 + j);
+            const unsigned bx = j < m1 ? 0u : (j < m2 ? 1u : 2u);
+            const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
+            const float ey = py - q.y;
+            const float ez = pz - q.z;
+            const float dd = ex * ex + ey * ey + ez * ez;
+            const unsigned code = (unsigned)(sg * 3 + (int)bx);
+            if (dd <= L2 && j != i) {  // within R + skin: listed for the steps until the rebuild
+              if (ln < kListCap) list[list_at(i, ln)] = (j << 5) | code;
+              ++ln;
+            }
+            s_cj[nc][t] = j;  // kept only if within R (every neighbour, band candidate and contact)
+            s_cc[nc][t] = (unsigned char)code;
+            nc += dd <= R2hi ? 1 : 0;
+            if constexpr (decltype(dense)::value) {
+              if (__any_sync(__activemask(), nc == kCL)) flush();
+            } else {
+              if (nc == kCL) flush();
+            }
+          }
+        };
+        if (__any_sync(__activemask(), e - a > 3u * kDenseBox)) run(std::true_type{});
+        else run(std::false_type{});
+      }
+      flush();
+      if (nband > (unsigned)kBQ) {
+        cnt = band_rescan(i, sx, sy, sz, p4, start, ix, iy, iz, d0, d1, d2, pi, Lf, R2lo, R2hi, R2);
+      } else {
+        for (unsigned k = 0; k < nband; ++k) cnt += fp64_within(i, s_bq[k][t], sx, sy, sz, R2);
+      }
+      cnt -= 1u;  // the agent itself
+      list_n[i] = ln < kListCap ? ln : kListCap;
+      if (ln > kListCap) g->list_overflow = 1u;  // the next step rebuilds again
+    } else {
+      // four entries at a time, their loads and their candidates' loads issued together, so the loop
+      // does not wait on one dependent load pair per entry
+      const unsigned m = __ldg(list_n + i);
+      for (unsigned k0 = 0; k0 < m; k0 += 4) {
+        unsigned v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = k0 + (unsigned)u < m ? __ldg(list + list_at(i, k0 + u)) : 0u;
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k0 + (unsigned)u < m) q[u] = __ldg(p4 + (v[u] >> 5));
+        // most listed candidates are neighbours: decided here, in list order, without staging
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (k0 + (unsigned)u >= m) break;
+          const unsigned j = v[u] >> 5, cc = v[u] & 31u;
+          const int sgk = (int)(cc / 3u), bxk = (int)(cc % 3u);
+          const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q[u].x;
+          const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q[u].y;
+          const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q[u].z;
+          const float dd = ex * ex + ey * ey + ez * ez;
+          if (dd <= R2hi) {
+            if (dd < R2lo) {
+              ++cnt;
+            } else {  // near R: queued for the FP64 decision after the loop
+              if (nband < (unsigned)kBQ) s_bq[nband][t] = j;
+              ++nband;
+            }
+            const float rs = pi.w + q[u].w;
+            if (dd < rs * rs && dd > 0.f)
+              contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q[u].w, c.kf, c.gammaf);
+          }
+        }
+      }
+      if (nband > (unsigned)kBQ) {
+        cnt = list_rescan(i, m, list, sx, sy, sz, p4, pi, Lf, R2lo, R2hi, R2);
+      } else {
+        for (unsigned k = 0; k < nband; ++k) cnt += fp64_within(i, s_bq[k][t], sx, sy, sz, R2);
+      }
+    }
+    float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
+    const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
+    if (n2 > c.capf * c.capf) {
+      const float f = c.capf * rsqrtf(n2);
+      Dx *= f; Dy *= f; Dz *= f;
+    }
+    ddx[i] = Dx;
+    ddy[i] = Dy;
+    ddz[i] = Dz;
+    nbr[i] = cnt;
+  }
+}
+
+// Lists of a rebuild step: the canonical 27-box walk on a grid of box length >= R + skin, keeping
+// every candidate within R + skin (no forces; the list kernel computes them from the lists).
+__global__ void __launch_bounds__(kBlock) k_list_build(const float4* __restrict__ p4,
+                                                       const unsigned* __restrict__ skey,
+                                                       const unsigned* __restrict__ start,
+                                                       unsigned* __restrict__ list,
+                                                       unsigned* __restrict__ list_n, DevGrid* g) {
+  if (!g->rebuild) return;
+  const unsigned n = g->nbox ? g->n : 0u;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const float Lf = g->Lf, L2 = g->list_L2f;
+  unsigned overflow = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned b = __ldg(skey + i);
+    const int ix = (int)(b % (unsigned)d0);
+    const unsigned q0 = b / (unsigned)d0;
+    const int iy = (int)(q0 % (unsigned)d1), iz = (int)(q0 / (unsigned)d1);
+    const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
+    const float4 pi = __ldg(p4 + i);
+    const float pxm = pi.x + Lf, px0 = pi.x, pxp = pi.x - Lf;
+    unsigned ln = 0;
+#pragma unroll 1
+    for (int sg = 0; sg < 9; ++sg) {
+      const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
+      if (jz < 0 || jz >= d2 || jy < 0 || jy >= d1) continue;
+      const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
+      const unsigned a = __ldg(start + row + xl);
+      const unsigned m1 = ix > 0 ? __ldg(start + row + ix) : a;
+      const unsigned m2 = __ldg(start + row + ix + 1);
+      const unsigned e = __ldg(start + row + xh + 1);
+      const float py = pi.y - (float)(sg % 3 - 1) * Lf, pz = pi.z - (float)(sg / 3 - 1) * Lf;
+      for (unsigned j = a; j < e; ++j) {
+        const float4 q = __ldg(p4 + j);
+        const unsigned bx = j < m1 ? 0u : (j < m2 ? 1u : 2u);
+        const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
+        const float ey = py - q.y;
+        const float ez = pz - q.z;
+        const float dd = ex * ex + ey * ey + ez * ez;
+        if (dd <= L2 && j != i) {
+          if (ln < kListCap) list[list_at(i, ln)] = (j << 5) | (unsigned)(sg * 3 + (int)bx);
+          ++ln;
+        }
+      }
+    }
+    list_n[i] = ln < kListCap ? ln : kListCap;
+    overflow |= ln > kListCap ? 1u : 0u;
+  }
+  if (overflow) g->list_overflow = 1u;  // this step's forces come from the walk, the next rebuilds
+}
+
+// In-place update of a neighbour-list step: FP64 centre += displacement (exact conversion, one FP64
+// add), FP32 offset += displacement, moves accumulated since the rebuild, the next step's bounds
+// and, on list steps, the box of each agent's step-start centre for the read-out (a rebuild's gather
+// has written it already).
+__global__ void __launch_bounds__(kBlock) k_apply_skin(
+    const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
+    double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
+    float4* __restrict__ p4, const float* __restrict__ ddx, const float* __restrict__ ddy,
+    const float* __restrict__ ddz, float* __restrict__ disp, unsigned* __restrict__ skey,
+    DevGrid* g) {
+  __shared__ unsigned s_dmax;
+  if (threadIdx.x == 0) s_dmax = 0u;
+  __syncthreads();
+  const unsigned n = g->nbox ? g->n : 0u;
+  const bool rb = g->rebuild != 0u;
+  const double* ax = rb ? sx : px;  // step-start centres: gathered on a rebuild, in place otherwise
+  const double* ay = rb ? sy : py;
+  const double* az = rb ? sz : pz;
+  const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const float inv = g->invLq;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  unsigned md = 0;
+  float dmax = 0.f;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double x0 = ax[i], y0 = ay[i], z0 = az[i];
+    const float Dx = ddx[i], Dy = ddy[i], Dz = ddz[i];
+    const double nx = __dadd_rn(x0, f2d_exact(Dx));
+    const double ny = __dadd_rn(y0, f2d_exact(Dy));
+    const double nz = __dadd_rn(z0, f2d_exact(Dz));
+    px[i] = nx;
+    py[i] = ny;
+    pz[i] = nz;
+    float4 q = p4[i];
+    q.x += Dx;
+    q.y += Dy;
+    q.z += Dz;
+    p4[i] = q;
+    const float D = (rb ? 0.f : disp[i]) + sqrtf(Dx * Dx + Dy * Dy + Dz * Dz);
+    disp[i] = D;
+    dmax = fmaxf(dmax, D);
+    if (!rb) {
+      int ix = box_div(quantise(x0) - O0, Lq, inv);
+      int iy = box_div(quantise(y0) - O1, Lq, inv);
+      int iz = box_div(quantise(z0) - O2, Lq, inv);
+      if (ix >= d0 || iy >= d1 || iz >= d2) {  // impossible by construction of the bounds
+        atomicOr(&g->err, (unsigned)ERR_BOUNDS);
+        ix = min(ix, d0 - 1); iy = min(iy, d1 - 1); iz = min(iz, d2 - 1);
+      }
+      skey[i] = (unsigned)ix + (unsigned)d0 * ((unsigned)iy + (unsigned)d1 * (unsigned)iz);
+    }
+    const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
+    mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
+    mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
+    mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
+    const unsigned dbits = __float_as_uint(2.0f * q.w);
+    md = dbits > md ? dbits : md;
+  }
+  // non-negative floats order like their bits
+  const unsigned wmax = warp_reduce(__float_as_uint(dmax), [](unsigned a, unsigned b) { return a > b ? a : b; });
+  if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_dmax, wmax);
+  block_commit_bounds<kBlock>(mn, mx, md, g);  // contains a __syncthreads
+  if (threadIdx.x == 0 && s_dmax) atomicMax(&g->max_disp, s_dmax);
+}
+
+// Keep one attribute buffer current: a rebuild's gather writes the canonical order into the other.
+__global__ void __launch_bounds__(kBlock) k_attr_copy(AgentArrays src, AgentArrays dst, DevGrid* g) {
+  const unsigned n = g->nbox ? g->n_sort : 0u;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    dst.diam[i] = src.diam[i];
+    dst.id[i] = src.id[i];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Force + capped update, mixed precision, warp-shared pairs (tunable alternative to one thread per
 // agent).  A warp owns 32 consecutive agents; for each of the nine rows the (agent, candidate)
 // pairs of all 32 agents are dealt out evenly over the lanes (owner table in shared memory), so
@@ -678,6 +1001,46 @@ void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr,
     k_force_fp64<<<grid_blocks, kF64, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, attr.diam,
                                                 b.skey, b.start, b.pos.x, b.pos.y, b.pos.z, b.nbr,
                                                 g, c);
+}
+
+void launch_force_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, MechConsts c, bool build,
+                       int grid_blocks) {
+  if (build)
+    k_force_skin<true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x,
+                                                   b.pos.y, b.pos.z, b.p4, b.skey, b.start, b.list,
+                                                   b.list_n, b.delta[0], b.delta[1], b.delta[2],
+                                                   b.nbr, g, c);
+  else
+    k_force_skin<false><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x,
+                                                    b.pos.y, b.pos.z, b.p4, b.skey, b.start, b.list,
+                                                    b.list_n, b.delta[0], b.delta[1], b.delta[2],
+                                                    b.nbr, g, c);
+}
+
+void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
+  k_list_build<<<grid_blocks, kBlock, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
+}
+
+void launch_apply_skin(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                       MechConsts c, int grid_blocks) {
+  (void)attr;
+  (void)c;
+  k_apply_skin<<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x, b.pos.y,
+                                              b.pos.z, b.p4, b.delta[0], b.delta[1], b.delta[2],
+                                              b.disp, b.skey, g);
+}
+
+void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
+                      int grid_blocks) {
+  k_attr_copy<<<grid_blocks, kBlock, 0, s>>>(src, dst, g);
+}
+
+int force_skin_blocks_per_sm() {
+  int a = 0, b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_force_skin<true>, kFT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force_skin<false>, kFT, 0);
+  const int m = a < b ? a : b;
+  return m > 0 ? m : 1;
 }
 
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -1,0 +1,119 @@
+"""Neighbour lists with a skin (mixed precision): the grid is rebuilt only when an agent may have
+moved more than skin / 2 since the last rebuild; the steps between evaluate each agent's listed
+candidates within R + skin.  Every step, from the GPU's own state, one oracle step must give the
+same grid assignment and neighbour counts bit for bit and positions within FP32 force error."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_06775_gb300 import bdm, synth
+
+pytestmark = pytest.mark.gpu
+
+R = 12.0
+
+
+def skin_params(skin, n=200_000, seed=31):
+    params, inp = synth.large_mechanics(n=n, seed=seed, with_grid=False)
+    return dict(params, interaction_radius=R, box_length=R + skin, skin=skin), inp
+
+
+def run_teacher_forced(params, inp, steps):
+    sim = bdm.Sim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    prev = sim.get_state()
+    worst = 0.0
+    for k in range(steps):
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle.mech_step(prev["x"], prev["y"], prev["z"], prev["diameter"], params["dt"],
+                                params["repulsion"], params["attraction"],
+                                params["max_displacement"], R, params["box_length"])
+        assert np.array_equal(got["box_id"], want["box_id"]), k
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        worst = max(worst, max(float(np.max(np.abs(got[a] - want[a]))) for a in ("x", "y", "z")))
+        prev = got
+    sim.close()
+    return worst, got["grid_rebuilds"]
+
+
+@pytest.mark.parametrize("skin,steps", [(0.8, 12), (3.0, 12)])
+def test_skin_steps_match_oracle_every_step(skin, steps):
+    params, inp = skin_params(skin)
+    worst, rebuilds = run_teacher_forced(params, inp, steps)
+    assert worst < 2e-5, worst
+    assert 1 <= rebuilds < steps  # lists were used between rebuilds
+    if skin >= 3.0:
+        assert rebuilds <= 4
+
+
+def test_skin_rebuilds_at_least_every_64_steps():
+    """A population at rest (spheres far apart): nothing moves, yet the grid is rebuilt every 64
+    steps, which bounds the FP32 drift of the listed offsets."""
+    g = np.random.default_rng(3)
+    n = 1000
+    x, y, z = (np.arange(n) % 10) * 30.0, (np.arange(n) // 10 % 10) * 30.0, (np.arange(n) // 100) * 30.0
+    d = np.full(n, 10.0, np.float32)
+    params = dict(synth.MECH_DEFAULTS, precision="mixed", interaction_radius=R, box_length=R + 2.0,
+                  skin=2.0)
+    sim = bdm.Sim(params)
+    sim.add_agents(x + g.uniform(0, 1, n), y, z, d)
+    sim.step(130)
+    st = sim.get_state(fields=("neighbour_count",))
+    assert st["grid_rebuilds"] == 3  # steps 0, 64, 128
+    assert st["neighbour_count"].sum() == 0
+
+
+def test_skin_agents_added_force_a_rebuild():
+    params, inp = skin_params(2.0, n=20_000, seed=32)
+    sim = bdm.Sim(dict(params, capacity=40_000))
+    ref = oracle.OracleSim(params)
+    half = 10_000
+    for s in (sim, ref):
+        s.add_agents(inp["x"][:half], inp["y"][:half], inp["z"][:half], inp["diameter"][:half])
+        s.step(3)
+    before = sim.get_state(fields=())["grid_rebuilds"]
+    for s in (sim, ref):
+        s.add_agents(inp["x"][half:], inp["y"][half:], inp["z"][half:], inp["diameter"][half:])
+    sim.step(1)
+    ref.step(1)
+    got, want = sim.get_state(), ref.get_state()
+    assert np.array_equal(got["neighbour_count"], want["neighbour_count"])
+    assert np.array_equal(got["box_id"], want["box_id"])
+    assert got["grid_rebuilds"] == before + 1
+
+
+@pytest.mark.parametrize("bad", [dict(precision="fp64"), dict(growth_enabled=1, capacity=10),
+                                 dict(box_length=R + 1.0), dict(force_variant=1), dict(skin=-1.0)])
+def test_skin_parameter_checks(bad):
+    params = dict(synth.MECH_DEFAULTS, precision="mixed", interaction_radius=R, box_length=R + 2.0,
+                  skin=2.0, growth_volume=1.0, division_volume=1.0)
+    with pytest.raises(bdm.BdmError):
+        bdm.Sim(dict(params, **bad))
+
+
+def test_skin_list_overflow_falls_back_to_the_walk():
+    """60 agents packed in a 10 um ball among sparse ones: each has more than 32 candidates within
+    R + skin, so the lists overflow; that step's forces come from the full walk and the next step
+    rebuilds again.  Every step still matches the oracle."""
+    g = np.random.default_rng(9)
+    core = g.uniform(-5, 5, (60, 3)) + 200.0
+    rest = g.uniform(0, 400, (3000, 3))
+    pts = np.concatenate([core, rest])
+    d = np.concatenate([np.full(60, 6.0), g.uniform(8, 12, 3000)]).astype(np.float32)
+    params = dict(synth.MECH_DEFAULTS, precision="mixed", interaction_radius=R, box_length=R + 2.0,
+                  skin=2.0)
+    sim = bdm.Sim(params)
+    sim.add_agents(pts[:, 0], pts[:, 1], pts[:, 2], d)
+    prev = sim.get_state()
+    for k in range(3):
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle.mech_step(prev["x"], prev["y"], prev["z"], prev["diameter"], params["dt"],
+                                params["repulsion"], params["attraction"],
+                                params["max_displacement"], R, params["box_length"])
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        assert np.array_equal(got["box_id"], want["box_id"]), k
+        assert max(float(np.max(np.abs(got[a] - want[a]))) for a in ("x", "y", "z")) < 2e-5
+        prev = got
+    assert got["grid_rebuilds"] == 3  # every step rebuilt
