@@ -39,6 +39,8 @@ KERNEL_BYTES = {
     "scatter": lambda B: 12 + 4 + 4 * B,         # key + rank in, starts, perm out
     "gather": lambda B: 44 + 48 + 4 * B,         # perm, key, payload (32) in; payload + skey + p4 out
     "force_mixed": lambda B: 44 + 28 + 4 * B,    # p4, FP64 centre, skey in; centre + count out
+    "force_list": lambda m: 36 + 4 * m,          # list (4 B per entry) + count + own p4 in;
+                                                 # displacement + neighbour count out
 }
 STEP_BYTES_PER_AGENT = lambda B: 4 * 32 + 8 * B  # rebuild + force + update, agent state S = 32 B
 # Algorithmic FP32 work of the force kernel: 9 FLOP per candidate pair of the 27-box search (3 sub,
@@ -227,6 +229,8 @@ def run_ours(args):
         knobs = tune.tune_mechanics(params, inp, inp["side"] ** 3, cache=cache)
     else:
         knobs = cache.get(tune.workload_signature(params, n, inp["side"] ** 3), tune.gpu_name())
+    if args.skin is not None:  # explicit sort cadence (neighbour-list skin, um) instead of the tuned one
+        knobs = dict(knobs or {"box_factor": 1.0, "force_variant": 0}, skin=args.skin)
     if knobs:
         params = tune.mechanics_params(params, inp, knobs)
     stream = torch.cuda.Stream()
@@ -275,25 +279,38 @@ def run_ours(args):
     per_launch = {k: v[1] / max(v[0], 1) for k, v in ktimes.items()}
     share = {k: v[1] for k, v in ktimes.items()}
     dom = max(share, key=lambda k: share[k])
-    # the force kernel is issue/ALU-bound (ncu: DRAM ~6% of peak, issue ~69% active): its roofline
-    # is FP32 arithmetic; the HBM view of the same launch is reported beside it
-    force_ms = per_launch.get("force_mixed", float("nan"))
-    flops = FORCE_FLOP_PER_AGENT(boxes_per_agent) * n
+    # the force kernels are issue/ALU-bound (ncu: DRAM well below peak, issue ~55-69 % active): the
+    # roofline is FP32 arithmetic; the HBM view of the same launch is reported beside it.  With a
+    # skin the dominant kernel evaluates neighbour lists (9 FLOP per listed pair + 13 per agent).
+    st1 = sim.get_state(fields=())
+    skin = float(params.get("skin", 0.0))
+    rebuilds_timed = int(st1["grid_rebuilds"]) - int(st0["grid_rebuilds"])
+    if skin > 0.0:
+        fkernel = "force_list"
+        per_agent = st1["list_entries"] / n
+        flop_pa = 9.0 * per_agent + 13.0
+        bytes_pa = KERNEL_BYTES["force_list"](per_agent)
+    else:
+        fkernel = "force_mixed"
+        flop_pa = FORCE_FLOP_PER_AGENT(boxes_per_agent)
+        bytes_pa = KERNEL_BYTES["force_mixed"](boxes_per_agent)
+    force_ms = per_launch.get(fkernel, float("nan"))
+    flops = flop_pa * n
     achieved_tf = flops / (force_ms * 1e-3) / 1e12
-    alg_bytes = KERNEL_BYTES["force_mixed"](boxes_per_agent) * n
+    alg_bytes = bytes_pa * n
     achieved_gb = alg_bytes / (force_ms * 1e-3) / 1e9
     mech_ms = sum(v[1] for k, v in ktimes.items() if k != "ftcs") / args.steps
     step_bytes = STEP_BYTES_PER_AGENT(boxes_per_agent) * n + 8.0 * 512 ** 3
     step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "force_mixed", "achieved": achieved_tf,
+    roofline = {"bound": "alu", "kernel": fkernel, "achieved": achieved_tf,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                "traffic": measured_traffic("force_mixed", n),
+                "traffic": measured_traffic(fkernel, n),
                 "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz)",
-                "alg_flop_per_agent": FORCE_FLOP_PER_AGENT(boxes_per_agent),
+                "alg_flop_per_agent": flop_pa,
                 "dominant_kernel_by_time": dom,
                 "hbm": {"achieved": achieved_gb, "peak": peak, "unit": "GB/s",
                         "frac": achieved_gb / peak, "peak_kind": peak_kind,
-                        "alg_bytes_per_agent": KERNEL_BYTES["force_mixed"](boxes_per_agent)}}
+                        "alg_bytes_per_agent": bytes_pa}}
 
     diffusion = None
     if "ftcs" in per_launch:
@@ -331,7 +348,12 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "agents": n, "grid": 512, "precision": "mixed",
                        "boxes_per_agent": round(boxes_per_agent, 4),
                        "tuned": ({"box_factor": knobs["box_factor"],
-                                  "force_variant": knobs["force_variant"]} if knobs else None),
+                                  "force_variant": knobs["force_variant"],
+                                  "skin": knobs.get("skin", 0.0)} if knobs else None),
+                       "sort_cadence": {"skin_um": skin,
+                                        "grid_rebuilds_in_timed_steps": rebuilds_timed,
+                                        "list_entries_per_agent": (st1["list_entries"] / n
+                                                                   if skin > 0.0 else None)},
                        "cache": "inputs larger than L2 (agent state ~12 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
@@ -546,6 +568,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", action="store_true",
                     help="re-measure the tunable knobs on this workload and cache the choice")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="neighbour-list skin in um (0: grid rebuilt every step); default: tuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-small", action="store_true",

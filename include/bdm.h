@@ -135,6 +135,7 @@ typedef struct bdm_state {
   int64_t grid_origin_q[3];      /* out: last grid origin, 2^-20 um lattice units (mechanics)      */
   int64_t grid_box_q;            /* out: box length, lattice units                                 */
   int64_t grid_dims[3];          /* out: boxes per axis                                            */
+  uint64_t list_entries;         /* out: listed candidates at the last rebuild (skin > 0)          */
 } bdm_state;
 
 typedef struct bdm_sim bdm_sim;

@@ -55,6 +55,7 @@ class State(ctypes.Structure):
         ("mass_total", ctypes.c_double), ("sir_counts", ctypes.c_uint32 * 3),
         ("grid_rebuilds", ctypes.c_uint32), ("grid_origin_q", ctypes.c_int64 * 3),
         ("grid_box_q", ctypes.c_int64), ("grid_dims", ctypes.c_int64 * 3),
+        ("list_entries", ctypes.c_uint64),
     ]
 
 
@@ -235,6 +236,7 @@ def bdm_get_state(h, fields=FIELDS, grid_size=0, out=None):
     res = dict(arrays)
     res.update(n=int(st2.n), step=int(st2.step), mass_total=float(st2.mass_total),
                sir_counts=np.array(st2.sir_counts[:], np.uint32), grid_rebuilds=int(st2.grid_rebuilds),
+               list_entries=int(st2.list_entries),
                grid_origin_q=np.array(st2.grid_origin_q[:], np.int64),
                grid_box_q=int(st2.grid_box_q), grid_dims=np.array(st2.grid_dims[:], np.int64))
     return res

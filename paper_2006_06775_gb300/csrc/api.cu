@@ -804,6 +804,7 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
   }
   st->grid_box_q = G.Lq;
   st->grid_rebuilds = G.rebuilds;
+  st->list_entries = G.list_entries;
   cudaStream_t sm = s->stream;
   if (s->is_sir) {
     const SirState& S = s->sb.a;

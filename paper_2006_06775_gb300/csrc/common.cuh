@@ -66,6 +66,7 @@ struct DevGrid {
   unsigned max_disp;              // float bits: max over agents of |moves| since the last rebuild
   unsigned since_rebuild;         // steps since the last rebuild
   unsigned rebuilds;              // rebuilds so far
+  unsigned long long list_entries;  // listed candidates of the last rebuild
   float list_L2f;                 // list radius squared (R + skin)^2, widened by 2^-10
   float Lf_list;                  // box length (um) of the grid the lists were built on
 };
@@ -116,16 +117,25 @@ __device__ __forceinline__ long long quantise(double v) {
   return (b >> 63) ? -(long long)q : (long long)q;
 }
 
-// Exact float -> double conversion with integer operations (normal numbers and zeros); other
-// encodings (subnormals, inf, NaN) take the conversion instruction.
+// Exact float -> double conversion with integer operations only (GB300's conversion instruction
+// runs on the slow FP64 pipe): zeros, subnormals (normalised with a leading-zero count) and normal
+// numbers; the displacements it converts are finite.
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
-  if (e == 0u || e == 0xFFu) return (double)f;
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
-                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  unsigned long long bits;
+  if (e != 0u) {  // normal: rebias the exponent 127 -> 1023, widen the mantissa
+    bits = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m != 0u) {  // subnormal m * 2^-149 with its leading one at bit p
+    const int p = 31 - __clz((int)m);
+    bits = ((unsigned long long)(p + 874) << 52) |
+           (((unsigned long long)m << (52 - p)) & 0x000FFFFFFFFFFFFFull);
+  } else {
+    bits = 0ull;
+  }
+  return __longlong_as_double((long long)(sign | bits));
 }
 
 // floor(D / Lq) for 0 <= D < 2^51, 0 < Lq < 2^40: a float estimate corrected by exact products.

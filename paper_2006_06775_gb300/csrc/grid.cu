@@ -103,6 +103,7 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
     g->since_rebuild = 0u;
     g->Lf_list = g->Lf;
     g->rebuilds += 1u;
+    g->list_entries = 0ull;
   } else {
     g->n_sort = 0u;
     g->nbox1_sort = 0u;

@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kBlock) k_list_build(const float4* __restrict_
   const unsigned n = g->nbox ? g->n : 0u;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const float Lf = g->Lf, L2 = g->list_L2f;
-  unsigned overflow = 0;
+  unsigned overflow = 0, listed = 0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned b = __ldg(skey + i);
     const int ix = (int)(b % (unsigned)d0);
@@ -535,8 +535,11 @@ __global__ void __launch_bounds__(kBlock) k_list_build(const float4* __restrict_
     }
     list_n[i] = ln < kListCap ? ln : kListCap;
     overflow |= ln > kListCap ? 1u : 0u;
+    listed += ln < kListCap ? ln : kListCap;
   }
   if (overflow) g->list_overflow = 1u;  // this step's forces come from the walk, the next rebuilds
+  listed = warp_reduce(listed, [](unsigned a, unsigned b) { return a + b; });
+  if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g->list_entries, (unsigned long long)listed);
 }
 
 // In-place update of a neighbour-list step: FP64 centre += displacement (exact conversion, one FP64

@@ -5,10 +5,13 @@ and SIR states are exact for every choice):
   mechanics   box_factor    grid box = factor x interaction radius (>= 1: the 27-box search stays
                             exact; bigger boxes mean fewer boxes but more candidates per agent)
               force_variant 0 = one thread per agent, 1 = warp-shared (agent, candidate) pairs
+              skin          sort cadence: 0 = grid rebuilt every step; s > 0 = neighbour lists of
+                            radius R + s, the grid rebuilt only when an agent may have moved more
+                            than s / 2 (the grid box is then R + s)
   SIR         sir_boxes     boxes per axis (a divisor of the lattice side with box >= r)
 
-The canonical (box, id) order is part of the model's definition here (it fixes the summation
-order), so the grid is rebuilt every step; there is no sort-cadence knob.
+The FP64 check path keeps the canonical (box, id) order of every step (it fixes the summation order
+that makes it bit-exact), so it always rebuilds every step.
 
 `tune_*` time each candidate for a few steps (CUDA events on the simulation's stream) and return
 the fastest; `TuneCache` keeps choices per (workload signature, GPU) in a small JSON file.
@@ -19,7 +22,10 @@ import os
 
 import numpy as np
 
-MECH_CANDIDATES = [dict(box_factor=f, force_variant=v) for v in (0, 1) for f in (1.0, 1.15, 1.3)]
+MECH_CANDIDATES = ([dict(box_factor=1.0, force_variant=0, skin=0.0),
+                    dict(box_factor=1.15, force_variant=0, skin=0.0),
+                    dict(box_factor=1.0, force_variant=1, skin=0.0)] +
+                   [dict(box_factor=1.0, force_variant=0, skin=s) for s in (1.5, 2.0, 2.5, 3.0)])
 
 
 def workload_signature(params, n, volume):
@@ -74,10 +80,11 @@ def mechanics_params(params, inputs, cand):
     R = params.get("interaction_radius") or float(np.max(inputs["diameter"]))
     p["box_length"] = cand["box_factor"] * R if cand["box_factor"] != 1.0 else 0.0
     p["force_variant"] = cand["force_variant"]
+    p["skin"] = cand.get("skin", 0.0)  # with a skin, box_length 0 means R + skin
     return p
 
 
-def gpu_measure_mechanics(params, inputs, steps=3, warmup=2):
+def gpu_measure_mechanics(params, inputs, steps=10, warmup=3):
     """Measurement function for `choose`: ms per step of one candidate on the GPU."""
     import torch
     from . import bdm
@@ -109,7 +116,8 @@ def tune_mechanics(params, inputs, volume, cache=None, measure=None, candidates=
     best, table = choose(candidates or MECH_CANDIDATES,
                          measure or gpu_measure_mechanics(params, inputs))
     choice = {"box_factor": best["box_factor"], "force_variant": best["force_variant"],
-              "ms_per_step": best["ms_per_step"], "table": table, "signature": sig}
+              "skin": best.get("skin", 0.0), "ms_per_step": best["ms_per_step"], "table": table,
+              "signature": sig}
     if cache is not None:
         cache.put(sig, gpu, choice)
     return choice
