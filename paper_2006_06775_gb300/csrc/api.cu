@@ -498,7 +498,7 @@ int enqueue_mech_step(bdm_sim* s) {
     RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_stream));
     RUN("force_walk", 1, launch_force_skin(st, b, g, s->mc, true, s->blocks_force));  // overflow only
     RUN("force_list", 1, launch_force_skin(st, b, g, s->mc, false, s->blocks_force));
-    RUN("apply", 1, launch_apply_skin(st, b, A, g, s->mc, s->blocks_stream));
+    RUN("apply", 1, launch_apply_skin(st, b, g, s->blocks_stream));
     s->bounds_fresh = true;  // attributes stay in A
   } else {
     RUN(s->mixed ? "force_mixed" : "force_fp64", 1, launch_force(st, b, B, g, s->mc, s->mixed, s->blocks_force));

@@ -263,13 +263,13 @@ void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr,
 int force_mixed_blocks_per_sm(int variant);
 int force_fp64_blocks(size_t capacity, int sms);  // grid of the FP64 force kernel
 constexpr unsigned kListCap = 32;  // listed candidates per agent (R + skin)
-// neighbour-list steps (mechanics.cu): the walk that also lists, the list-driven force, the in-place
-// update, and the attribute copy that keeps one attribute buffer current
+// neighbour-list steps (mechanics.cu): the list build of a rebuild step, the list-driven force (or
+// the walk when a list overflowed), the in-place update, and the attribute copy that keeps one
+// attribute buffer current
 void launch_force_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, MechConsts c, bool build,
                        int grid_blocks);
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
-void launch_apply_skin(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
-                       MechConsts c, int grid_blocks);
+void launch_apply_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
                       int grid_blocks);
 int force_skin_blocks_per_sm();

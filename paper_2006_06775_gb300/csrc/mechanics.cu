@@ -291,14 +291,15 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
 }
 
 // ---------------------------------------------------------------------------------------------
-// Neighbour-list steps (skin > 0).  A rebuild step runs the canonical 27-box walk of k_force_mixed
-// on a grid whose box length is at least R + skin, and also lists, per agent, every candidate within
-// R + skin ((j << 5) | (row * 3 + box x), in canonical order).  The steps between evaluate those
-// lists instead of walking the grid: while no agent has moved more than skin / 2, every pair
-// within R was within R + skin at the rebuild, so every neighbour and contact is listed.  Counts use
-// the same FP32 band + FP64 decision as the walk, so they stay exact; the FP32 force sums follow
-// the list (the canonical order of the last rebuild).  Both kernels write the capped displacement;
-// k_apply_skin then moves the FP64 centres and FP32 offsets in place.
+// Neighbour-list steps (skin > 0).  A rebuild step lists, per agent, every candidate within R + skin
+// found by the canonical 27-box walk on a grid whose box length is at least R + skin
+// ((j << 5) | (row * 3 + box x), in canonical order: k_list_build).  Every step then evaluates the
+// lists (k_force_skin<false>): while no agent has moved more than skin / 2 since the rebuild, every
+// pair within R was within R + skin at the rebuild, so every neighbour and contact is listed.
+// Counts use the same FP32 band + FP64 decision as the walk, so they stay exact; the FP32 force sums
+// follow the list (the canonical order of the last rebuild).  If a list overflowed, that step's
+// forces come from the walk itself (k_force_skin<true>) and the next step rebuilds.  Both write the
+// capped displacement; k_apply_skin then moves the FP64 centres and FP32 offsets in place.
 // ---------------------------------------------------------------------------------------------
 
 // List layout: the entries of the 32 agents of one warp-sized group are interleaved, entry k of agent
@@ -1024,10 +1025,7 @@ void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int gri
   k_list_build<<<grid_blocks, kBlock, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
 }
 
-void launch_apply_skin(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
-                       MechConsts c, int grid_blocks) {
-  (void)attr;
-  (void)c;
+void launch_apply_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
   k_apply_skin<<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x, b.pos.y,
                                               b.pos.z, b.p4, b.delta[0], b.delta[1], b.delta[2],
                                               b.disp, b.skey, g);
