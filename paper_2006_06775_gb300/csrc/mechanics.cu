@@ -191,6 +191,14 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
   const float Lf = g->Lf, R2lo = g->R2lo, R2hi = g->R2hi;
   unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
   unsigned md = 0;
+  // candidate offset shift of each box code (row * 3 + box x): exact multiples of the box length
+  __shared__ float4 s_shift[27];
+  if (threadIdx.x < 27) {
+    const int row = threadIdx.x / 3, bx = threadIdx.x % 3;
+    s_shift[threadIdx.x] = make_float4(-(float)(bx - 1) * Lf, -(float)(row % 3 - 1) * Lf,
+                                       -(float)(row / 3 - 1) * Lf, 0.f);
+  }
+  __syncthreads();
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned b = __ldg(skey + i);
     const int ix = (int)(b % (unsigned)d0);
@@ -211,10 +219,10 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
       for (int k = 0; k < nc; ++k) {
         const unsigned cj = s_cj[k][t], cc = s_cc[k][t];
         const float4 q = __ldg(p4 + cj);
-        const int sgk = (int)(cc / 3u), bxk = (int)(cc % 3u);
-        const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q.x;
-        const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
-        const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
+        const float4 sh = s_shift[cc];
+        const float ex = (pi.x + sh.x) - q.x;
+        const float ey = (pi.y + sh.y) - q.y;
+        const float ez = (pi.z + sh.z) - q.z;
         const float dd = ex * ex + ey * ey + ez * ez;
         if (dd < R2lo) {
           ++cnt;
@@ -357,6 +365,14 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   const double R2 = g->R2;
   const float Lf = BUILD ? g->Lf : g->Lf_list, R2lo = g->R2lo, R2hi = g->R2hi, L2 = g->list_L2f;
   const int t = threadIdx.x;
+  // candidate offset shift of each box code (row * 3 + box x): exact multiples of the box length
+  __shared__ float4 s_shift[27];
+  if (t < 27) {
+    const int row = t / 3, bx = t % 3;
+    s_shift[t] = make_float4(-(float)(bx - 1) * Lf, -(float)(row % 3 - 1) * Lf,
+                             -(float)(row / 3 - 1) * Lf, 0.f);
+  }
+  __syncthreads();
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float4 pi = __ldg(p4 + i);
     const float pxm = pi.x + Lf, px0 = pi.x, pxp = pi.x - Lf;  // neighbour box at x-1, x, x+1
@@ -453,10 +469,10 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
         for (int u = 0; u < 4; ++u) {
           if (k0 + (unsigned)u >= m) break;
           const unsigned j = v[u] >> 5, cc = v[u] & 31u;
-          const int sgk = (int)(cc / 3u), bxk = (int)(cc % 3u);
-          const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q[u].x;
-          const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q[u].y;
-          const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q[u].z;
+          const float4 sh = s_shift[cc];
+          const float ex = (pi.x + sh.x) - q[u].x;
+          const float ey = (pi.y + sh.y) - q[u].y;
+          const float ez = (pi.z + sh.z) - q[u].z;
           const float dd = ex * ex + ey * ey + ez * ez;
           if (dd <= R2hi) {
             if (dd < R2lo) {
