@@ -444,10 +444,33 @@ def bench_plain(steps=10, reps=50):
             for _ in range(reps):
                 sim.step(steps)
         ms = _event_time_ms(sim.stream, run)
+        st = sim.get_state(fields=("neighbour_count",))
         sim.close()
         out[prec] = {"agent_steps_per_s": 4096 * steps * reps / (ms * 1e-3),
                      "ms_per_step": ms / (steps * reps)}
+        if prec == "fp64":
+            # the FP64 path is bound by GB300's FP64 arithmetic: its algorithmic FP64 work (9 per
+            # candidate pair of the 27-box search, ~25 per contact) against the FP64 peak measured here
+            nbox = int(np.prod(st["grid_dims"]))
+            flop_pa = 9.0 * 27.0 * 4096 / nbox + 25.0 * float(st["neighbour_count"].mean())
+            peak = fp64_peak_tflops()
+            achieved = 4096 * flop_pa / (out[prec]["ms_per_step"] * 1e-3) / 1e12
+            out[prec]["roofline"] = {"bound": "fp64", "alg_flop_per_agent": flop_pa,
+                                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak,
+                                     "peak_kind": "measured: cuBLAS DGEMM 4096^3 on this GPU"}
     return out
+
+
+def fp64_peak_tflops(n=4096, reps=5):
+    """FP64 arithmetic peak of this GPU as cuBLAS reaches it (DGEMM), in TFLOP/s."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    stream = torch.cuda.current_stream()
+    ms = _event_time_ms(stream, lambda: [torch.matmul(a, b) for _ in range(reps)])
+    return 2.0 * n ** 3 * reps / (ms * 1e-3) / 1e12
 
 
 def bench_spheroid(max_agents=1_000_000, max_steps=160):
