@@ -113,7 +113,9 @@ typedef struct bdm_params {
 } bdm_params;
 
 /* Read-out of one simulation.  Set struct_size; every pointer may be NULL (field skipped); buffers
- * must hold at least `n` entries (query n first with all pointers NULL), grid prod(grid_n). */
+ * must hold at least `n` entries (query n first with all pointers NULL), grid prod(grid_n).  A
+ * field that the handle's kind does not hold (diameter and volume for SIR; sir_state for
+ * mechanics; volume without growth) is not written: its buffer keeps what the caller put there. */
 typedef struct bdm_state {
   uint32_t struct_size;          /* = sizeof(bdm_state)                                            */
   uint32_t reserved0;

@@ -468,7 +468,22 @@ class Sim:
     def diffusion_step(self, n=1):
         bdm_diffusion_step(self.h, n)
 
-    def get_state(self, fields=FIELDS, out=None):
+    def state_fields(self):
+        """The fields this handle writes: no diameter or volume for SIR, no SIR state for
+        mechanics, and volume only with growth."""
+        if self.params.get("kind", "mechanics") in ("sir", BDM_SIR):
+            skip = {"diameter", "volume"}
+        else:
+            skip = {"sir_state"} | (set() if self.params.get("growth_enabled") else {"volume"})
+        return tuple(f for f in FIELDS if f not in skip)
+
+    def get_state(self, fields=None, out=None):
+        have = self.state_fields()
+        if fields is None:
+            fields = have
+        missing = [f for f in fields if f not in have and f != "grid"]
+        if missing:
+            raise ValueError("this handle does not hold %s" % ", ".join(missing))
         return bdm_get_state(self.h, fields, self.grid_size, out)
 
     def profile(self, enable=True):

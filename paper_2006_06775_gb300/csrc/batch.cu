@@ -162,6 +162,8 @@ int build(bdm_batch* b) {
   }
   // start/perm/src are zeroed so that every index a step can read is in range even when a bounded
   // barrier wait gives up before the phase that writes them has finished
+  // the first step's scan needs clear tile flags; later steps clear them after their own scan
+  BCK(cudaMemsetAsync(D.tiles, 0, sizeof(unsigned long long) * D.max_tiles, s));
   BCK(cudaMemsetAsync(D.count, 0, 4 * (boxes + 1), s));
   BCK(cudaMemsetAsync(D.start, 0, 4 * (boxes + 1), s));
   BCK(cudaMemsetAsync(D.perm, 0, 4 * A, s));
