@@ -85,7 +85,7 @@ struct Profiler {
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   unsigned long long kernels = 0;
-  int attr_cur = 0, grid_cur = 0;
+  int attr_cur = 0, grid_cur = 0, pos_cur = 0;
   bool bounds_fresh = false;
 };
 
@@ -110,6 +110,7 @@ struct bdm_sim {
   MechBuffers mb{};
   MechConsts mc{};
   int attr_cur = 0;
+  int pos_cur = 0;          // skin > 0: the position set holding the current agents
   bool bounds_fresh = false;
   float* grid[2] = {nullptr, nullptr};
   int grid_cur = 0;
@@ -119,12 +120,12 @@ struct bdm_sim {
   SirSingle sb{};
   std::vector<void*> allocs;
   // n-step graphs keyed by (steps, diffusion only, attr parity, grid parity, bounds fresh, SIR
-  // agent count): each key fixes every pointer and launch size the capture saw
-  std::map<std::tuple<int, int, int, int, int, size_t>, GraphEntry> graphs;
+  // agent count, position-set parity): each key fixes every pointer and launch size the capture saw
+  std::map<std::tuple<int, int, int, int, int, size_t, int>, GraphEntry> graphs;
   Profiler prof;
   bool capturing = false;
   unsigned long long capture_kernels = 0;
-  int blocks_stream = 1216, blocks_force = 608, blocks_scan = 608;
+  int blocks_stream = 1216, blocks_force = 608, blocks_walk = 608, blocks_scan = 608;
   unsigned n_stage = 0;     // host source of the agent-count upload
 };
 
@@ -358,11 +359,14 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
         (rc = dalloc_n(s, &b.start, boxcap + 1)))
       return rc;
     if (s->mixed && (rc = dalloc_n(s, &b.p4, C))) return rc;
+    b.pset[0] = b.pos;
+    b.p4set[0] = b.p4;
     if (p.skin > 0.0) {
       if (C >= (1ull << 27)) return fail(s, BDM_EINVAL, "a neighbour-list skin supports up to 2^27 agents");
       if ((rc = dalloc_n(s, &b.list, (size_t)kListCap * ((C + 31) / 32 * 32))) || (rc = dalloc_n(s, &b.list_n, C)) ||
-          (rc = dalloc_n(s, &b.disp, C)) || (rc = dalloc_n(s, &b.delta[0], C)) ||
-          (rc = dalloc_n(s, &b.delta[1], C)) || (rc = dalloc_n(s, &b.delta[2], C)))
+          (rc = dalloc_n(s, &b.disp, C)) || (rc = dalloc_n(s, &b.pset[1].x, C)) ||
+          (rc = dalloc_n(s, &b.pset[1].y, C)) || (rc = dalloc_n(s, &b.pset[1].z, C)) ||
+          (rc = dalloc_n(s, &b.p4set[1], C)))
         return rc;
       CK(cudaMemsetAsync(b.list_n, 0, sizeof(unsigned) * C, s->stream));
       CK(cudaMemsetAsync(b.disp, 0, sizeof(float) * C, s->stream));
@@ -412,9 +416,10 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
   const int stream_blocks = s->sms * 8;
   const size_t need = (C + kBlock - 1) / kBlock;
   s->blocks_stream = (int)std::max<size_t>(1, std::min<size_t>(need, stream_blocks));
-  s->blocks_force = s->mixed ? s->sms * (p.skin > 0.0 ? force_skin_blocks_per_sm()
+  s->blocks_force = s->mixed ? s->sms * (p.skin > 0.0 ? force_skin_blocks_per_sm(false)
                                                       : force_mixed_blocks_per_sm(s->mc.force_variant))
                              : force_fp64_blocks(C, s->sms);
+  s->blocks_walk = p.skin > 0.0 ? s->sms * force_skin_blocks_per_sm(true) : s->blocks_force;
   const size_t tiles = s->is_sir ? s->sb.max_tiles : s->mb.max_tiles;
   s->blocks_scan = (int)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)s->sms * 4));
   s->allocated = true;
@@ -462,6 +467,16 @@ int enqueue_diffusion(bdm_sim* s) {
   return BDM_OK;
 }
 
+// Point the current-position views at position set pos_cur (two sets only with a skin).
+void point_current(bdm_sim* s) {
+  MechBuffers& b = s->mb;
+  if (!b.pset[1].x) return;
+  b.pos.x = b.pset[s->pos_cur].x;
+  b.pos.y = b.pset[s->pos_cur].y;
+  b.pos.z = b.pset[s->pos_cur].z;
+  b.p4 = b.p4set[s->pos_cur];
+}
+
 int enqueue_mech_step(bdm_sim* s) {
   cudaStream_t st = s->stream;
   const bdm_params& p = s->p;
@@ -496,9 +511,10 @@ int enqueue_mech_step(bdm_sim* s) {
   if (s->mc.skin > 0.0) {
     RUN("attr_copy", 1, launch_attr_copy(st, B, A, g, s->blocks_stream));
     RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_stream));
-    RUN("force_walk", 1, launch_force_skin(st, b, g, s->mc, true, s->blocks_force));  // overflow only
-    RUN("force_list", 1, launch_force_skin(st, b, g, s->mc, false, s->blocks_force));
-    RUN("apply", 1, launch_apply_skin(st, b, g, s->blocks_stream));
+    RUN("force_walk", 1, launch_force_skin(st, b, s->pos_cur, g, s->mc, true, s->blocks_walk));  // overflow only
+    RUN("force_list", 1, launch_force_skin(st, b, s->pos_cur, g, s->mc, false, s->blocks_force));
+    s->pos_cur ^= 1;  // the force kernels wrote the step's result into the other position set
+    point_current(s);
     s->bounds_fresh = true;  // attributes stay in A
   } else {
     RUN(s->mixed ? "force_mixed" : "force_fp64", 1, launch_force(st, b, B, g, s->mc, s->mixed, s->blocks_force));
@@ -535,11 +551,11 @@ int enqueue_steps(bdm_sim* s, int n, bool diffusion_only) {
 int launch_steps(bdm_sim* s, int n, bool diffusion_only) {
   if (s->prof.on) return enqueue_steps(s, n, diffusion_only);
   const auto key = std::make_tuple(n, (int)diffusion_only, s->attr_cur, s->grid_cur,
-                                   (int)s->bounds_fresh, s->is_sir ? s->n_host : (size_t)0);
+                                   (int)s->bounds_fresh, s->is_sir ? s->n_host : (size_t)0, s->pos_cur);
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
     GraphEntry ge;
-    const int a0 = s->attr_cur, g0 = s->grid_cur;
+    const int a0 = s->attr_cur, g0 = s->grid_cur, p0 = s->pos_cur;
     const bool f0 = s->bounds_fresh;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     s->capturing = true;
@@ -560,9 +576,12 @@ int launch_steps(bdm_sim* s, int n, bool diffusion_only) {
     ge.attr_cur = s->attr_cur;
     ge.grid_cur = s->grid_cur;
     ge.bounds_fresh = s->bounds_fresh;
+    ge.pos_cur = s->pos_cur;
     s->attr_cur = a0;
     s->grid_cur = g0;
     s->bounds_fresh = f0;
+    s->pos_cur = p0;
+    point_current(s);
     if (s->graphs.size() > 64) {
       for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second.exec);
       s->graphs.clear();
@@ -574,6 +593,8 @@ int launch_steps(bdm_sim* s, int n, bool diffusion_only) {
   s->attr_cur = it->second.attr_cur;
   s->grid_cur = it->second.grid_cur;
   s->bounds_fresh = it->second.bounds_fresh;
+  s->pos_cur = it->second.pos_cur;
+  point_current(s);
   return BDM_OK;
 }
 

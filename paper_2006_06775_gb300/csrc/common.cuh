@@ -167,6 +167,21 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
   return c;
 }
 
+// ---- asynchronous global -> shared copies (per thread; completion by commit / wait groups) ------
+// Both addresses must be aligned to the copy size.  A thread reads what it copied only after a
+// wait that covers the copy's group.
+template <int B>
+__device__ __forceinline__ void cp_async_n(void* smem, const void* gmem) {
+  static_assert(B == 4 || B == 8 || B == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ---- block reductions -------------------------------------------------------------------------
 template <typename T, typename Op>
 __device__ __forceinline__ T warp_reduce(T v, Op op) {
@@ -229,11 +244,15 @@ struct AgentArrays {             // one SoA buffer of agents
 };
 
 struct MechBuffers {
-  AgentArrays pos;               // P0: current positions (x,y,z used) -- always the step's output
-  AgentArrays sorted;            // P1: positions gathered into canonical order (x,y,z used)
+  AgentArrays pos;               // current positions (x,y,z used); with a skin = pset[current]
+  AgentArrays sorted;            // positions gathered into canonical order (x,y,z used)
+  // skin > 0: two position sets that alternate every step (x,y,z and the offsets p4set), the
+  // list kernels read one and write the other; without a skin pset[0] = pos and p4set[0] = p4
+  AgentArrays pset[2];
+  float4* p4set[2];
   AgentArrays attr[2];           // diam/id/vol, ping-pong by step parity
   unsigned *key, *rank, *perm, *skey, *nbr, *count, *start;
-  float4* p4;                    // mixed: box-relative offsets + radius, canonical order
+  float4* p4;                    // mixed: box-relative offsets + radius (= p4set[current])
   unsigned long long* tiles[2];  // scan tile states (box scan, division scan)
   unsigned* flag;                // growth: divide flags by id; also the division rank array
   unsigned* drank;
@@ -243,7 +262,6 @@ struct MechBuffers {
   unsigned* list;
   unsigned* list_n;
   float* disp;                   // |moves| of each agent since the last rebuild
-  float* delta[3];               // this step's capped displacement
 };
 
 // grid.cu
@@ -266,13 +284,12 @@ constexpr unsigned kListCap = 32;  // listed candidates per agent (R + skin)
 // neighbour-list steps (mechanics.cu): the list build of a rebuild step, the list-driven force (or
 // the walk when a list overflowed), the in-place update, and the attribute copy that keeps one
 // attribute buffer current
-void launch_force_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, MechConsts c, bool build,
-                       int grid_blocks);
+void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g, MechConsts c,
+                       bool build, int grid_blocks);
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
-void launch_apply_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
                       int grid_blocks);
-int force_skin_blocks_per_sm();
+int force_skin_blocks_per_sm(bool build);
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                  double dv, double vdiv, int grid_blocks);
 void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
 // pair within R was within R + skin at the rebuild, so every neighbour and contact is listed.
 // Counts use the same FP32 band + FP64 decision as the walk, so they stay exact; the FP32 force sums
 // follow the list (the canonical order of the last rebuild).  If a list overflowed, that step's
-// forces come from the walk itself (k_force_skin<true>) and the next step rebuilds.  Both write the
-// capped displacement; k_apply_skin then moves the FP64 centres and FP32 offsets in place.
+// forces come from the walk itself (k_force_skin<true>) and the next step rebuilds.  Both apply the
+// capped displacement themselves, into the other of two alternating position sets.
 // ---------------------------------------------------------------------------------------------
 
 // List layout: the entries of the 32 agents of one warp-sized group are interleaved, entry k of agent
@@ -341,23 +341,40 @@ __device__ __noinline__ unsigned list_rescan(unsigned i, unsigned m, const unsig
   return k;
 }
 
+// Positions of a list step live in two sets that alternate every step (centres FP64, offsets FP32):
+// the kernel reads the current set and writes the next, so every neighbour read sees step-start
+// values while each agent's own update is written at once (no separate update pass).  On a rebuild
+// step the centres come from the gather's set and the offsets from the current set's offset buffer,
+// which the gather has overwritten in canonical order.
 template <bool BUILD>
 __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     const double* __restrict__ gx, const double* __restrict__ gy, const double* __restrict__ gz,
     const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pz,
-    const float4* __restrict__ p4, const unsigned* __restrict__ skey,
+    const float4* __restrict__ p4, double* __restrict__ ox, double* __restrict__ oy,
+    double* __restrict__ oz, float4* __restrict__ op4, unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, unsigned* __restrict__ list, unsigned* __restrict__ list_n,
-    float* __restrict__ ddx, float* __restrict__ ddy, float* __restrict__ ddz,
-    unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
+    float* __restrict__ disp, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
   // BUILD: the walk with forces, only on a rebuild step whose lists overflowed; otherwise the lists
   // (built by k_list_build on a rebuild step) give the forces
   if (BUILD ? !(g->rebuild && g->list_overflow) : g->list_overflow != 0u) return;
   __shared__ unsigned s_cj[kCL][kFT];       // candidate list: index
   __shared__ unsigned char s_cc[kCL][kFT];  // candidate list: row segment * 3 + box x
   __shared__ unsigned s_bq[kBQ][kFT];       // band queue: candidates decided in FP64 after the loop
+  // per-thread bounds of the new centres, largest diameter and move since the rebuild (kept in
+  // shared memory: the loop already uses every register the occupancy target allows)
+  __shared__ unsigned long long s_mn[3][kFT], s_mx[3][kFT];
+  __shared__ unsigned s_md[kFT];
+  __shared__ float s_dm[kFT];
+  // list steps: the next agent's offsets, list length and first four entries are copied ahead
+  // (double-buffered), and this agent's FP64 centre and move arrive during its force loop
+  __shared__ float4 s_pi[2][kFT];
+  __shared__ unsigned s_m[2][kFT];
+  __shared__ unsigned s_v[2][4][kFT];
+  __shared__ double s_c[3][kFT];
+  __shared__ float s_d[kFT];
   const unsigned n = g->nbox ? g->n : 0u;
   const bool rb = g->rebuild != 0u;
-  // step-start centres: gathered on a rebuild step, in place otherwise
+  // step-start centres: gathered on a rebuild step, the current set otherwise
   const double* __restrict__ sx = rb ? gx : px;
   const double* __restrict__ sy = rb ? gy : py;
   const double* __restrict__ sz = rb ? gz : pz;
@@ -372,9 +389,41 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     s_shift[t] = make_float4(-(float)(bx - 1) * Lf, -(float)(row % 3 - 1) * Lf,
                              -(float)(row / 3 - 1) * Lf, 0.f);
   }
+  for (int a = 0; a < 3; ++a) {
+    s_mn[a][t] = ~0ull;
+    s_mx[a][t] = 0ull;
+  }
+  s_md[t] = 0u;
+  s_dm[t] = 0.f;
   __syncthreads();
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float4 pi = __ldg(p4 + i);
+  const unsigned stride = gridDim.x * blockDim.x;
+  auto prefetch = [&](unsigned a, int b) {  // list step: agent a's offsets, list length, entries 0-3
+    cp_async_n<16>(&s_pi[b][t], p4 + a);
+    cp_async_n<4>(&s_m[b][t], list_n + a);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cp_async_n<4>(&s_v[b][u][t], list + list_at(a, (unsigned)u));
+  };
+  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  int buf = 0;
+  if constexpr (!BUILD) {
+    if (i < n) prefetch(i, 0);
+    cp_async_commit();
+  }
+  for (; i < n; i += stride) {
+    float4 pi;
+    if constexpr (BUILD) {
+      pi = __ldg(p4 + i);
+    } else {
+      cp_async_n<8>(&s_c[0][t], sx + i);
+      cp_async_n<8>(&s_c[1][t], sy + i);
+      cp_async_n<8>(&s_c[2][t], sz + i);
+      cp_async_n<4>(&s_d[t], disp + i);
+      cp_async_commit();
+      if (i + stride < n) prefetch(i + stride, buf ^ 1);
+      cp_async_commit();
+      cp_async_wait<2>();  // this agent's prefetch (issued one iteration earlier) has landed
+      pi = s_pi[buf][t];
+    }
     const float pxm = pi.x + Lf, px0 = pi.x, pxp = pi.x - Lf;  // neighbour box at x-1, x, x+1
     unsigned cnt = 0;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
@@ -455,11 +504,17 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     } else {
       // four entries at a time, their loads and their candidates' loads issued together, so the loop
       // does not wait on one dependent load pair per entry
-      const unsigned m = __ldg(list_n + i);
+      const unsigned m = s_m[buf][t];
       for (unsigned k0 = 0; k0 < m; k0 += 4) {
         unsigned v[4];
+        if (k0 == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = k0 + (unsigned)u < m ? __ldg(list + list_at(i, k0 + u)) : 0u;
+          for (int u = 0; u < 4; ++u) v[u] = s_v[buf][u][t];
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            v[u] = k0 + (unsigned)u < m ? __ldg(list + list_at(i, k0 + u)) : 0u;
+        }
         float4 q[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -499,11 +554,68 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
       const float f = c.capf * rsqrtf(n2);
       Dx *= f; Dy *= f; Dz *= f;
     }
-    ddx[i] = Dx;
-    ddy[i] = Dy;
-    ddz[i] = Dz;
     nbr[i] = cnt;
+    // update: FP64 centre += displacement (exact conversion, one FP64 add), FP32 offset +=
+    // displacement, move since the rebuild; on a list step also the box of the step-start centre
+    // for the read-out (a rebuild's gather has written it already)
+    double x0, y0, z0;
+    float dprev = 0.f;
+    if constexpr (BUILD) {
+      x0 = sx[i];
+      y0 = sy[i];
+      z0 = sz[i];
+    } else {
+      cp_async_wait<1>();  // this agent's centre and move (the newest group is the next prefetch)
+      x0 = s_c[0][t];
+      y0 = s_c[1][t];
+      z0 = s_c[2][t];
+      dprev = s_d[t];
+      buf ^= 1;
+    }
+    const double nx = __dadd_rn(x0, f2d_exact(Dx));
+    const double ny = __dadd_rn(y0, f2d_exact(Dy));
+    const double nz = __dadd_rn(z0, f2d_exact(Dz));
+    ox[i] = nx;
+    oy[i] = ny;
+    oz[i] = nz;
+    op4[i] = make_float4(pi.x + Dx, pi.y + Dy, pi.z + Dz, pi.w);
+    const float D = (rb ? 0.f : dprev) + sqrtf(Dx * Dx + Dy * Dy + Dz * Dz);
+    disp[i] = D;
+    s_dm[t] = fmaxf(s_dm[t], D);
+    if (!BUILD && !rb) {
+      const long long Lq = g->Lq;
+      const float inv = g->invLq;
+      int bx = box_div(quantise(x0) - g->O[0], Lq, inv);
+      int by = box_div(quantise(y0) - g->O[1], Lq, inv);
+      int bz = box_div(quantise(z0) - g->O[2], Lq, inv);
+      if (bx >= d0 || by >= d1 || bz >= d2) {  // impossible by construction of the bounds
+        atomicOr(&g->err, (unsigned)ERR_BOUNDS);
+        bx = min(bx, d0 - 1); by = min(by, d1 - 1); bz = min(bz, d2 - 1);
+      }
+      skey[i] = (unsigned)bx + (unsigned)d0 * ((unsigned)by + (unsigned)d1 * (unsigned)bz);
+    }
+    const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
+    s_mn[0][t] = e0 < s_mn[0][t] ? e0 : s_mn[0][t];
+    s_mx[0][t] = e0 > s_mx[0][t] ? e0 : s_mx[0][t];
+    s_mn[1][t] = e1 < s_mn[1][t] ? e1 : s_mn[1][t];
+    s_mx[1][t] = e1 > s_mx[1][t] ? e1 : s_mx[1][t];
+    s_mn[2][t] = e2 < s_mn[2][t] ? e2 : s_mn[2][t];
+    s_mx[2][t] = e2 > s_mx[2][t] ? e2 : s_mx[2][t];
+    const unsigned dbits = __float_as_uint(2.0f * pi.w);
+    s_md[t] = dbits > s_md[t] ? dbits : s_md[t];
   }
+  if constexpr (!BUILD) cp_async_wait<0>();
+  __shared__ unsigned s_dmax;
+  if (t == 0) s_dmax = 0u;
+  __syncthreads();
+  // non-negative floats order like their bits
+  const unsigned wmax =
+      warp_reduce(__float_as_uint(s_dm[t]), [](unsigned a, unsigned b) { return a > b ? a : b; });
+  if ((t & 31) == 0 && wmax) atomicMax(&s_dmax, wmax);
+  unsigned long long mn[3] = {s_mn[0][t], s_mn[1][t], s_mn[2][t]};
+  unsigned long long mx[3] = {s_mx[0][t], s_mx[1][t], s_mx[2][t]};
+  block_commit_bounds<kFT>(mn, mx, s_md[t], g);  // contains a __syncthreads
+  if (t == 0 && s_dmax) atomicMax(&g->max_disp, s_dmax);
 }
 
 // Lists of a rebuild step: the canonical 27-box walk on a grid of box length >= R + skin, keeping
@@ -557,71 +669,6 @@ __global__ void __launch_bounds__(kBlock) k_list_build(const float4* __restrict_
   if (overflow) g->list_overflow = 1u;  // this step's forces come from the walk, the next rebuilds
   listed = warp_reduce(listed, [](unsigned a, unsigned b) { return a + b; });
   if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g->list_entries, (unsigned long long)listed);
-}
-
-// In-place update of a neighbour-list step: FP64 centre += displacement (exact conversion, one FP64
-// add), FP32 offset += displacement, moves accumulated since the rebuild, the next step's bounds
-// and, on list steps, the box of each agent's step-start centre for the read-out (a rebuild's gather
-// has written it already).
-__global__ void __launch_bounds__(kBlock) k_apply_skin(
-    const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
-    double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
-    float4* __restrict__ p4, const float* __restrict__ ddx, const float* __restrict__ ddy,
-    const float* __restrict__ ddz, float* __restrict__ disp, unsigned* __restrict__ skey,
-    DevGrid* g) {
-  __shared__ unsigned s_dmax;
-  if (threadIdx.x == 0) s_dmax = 0u;
-  __syncthreads();
-  const unsigned n = g->nbox ? g->n : 0u;
-  const bool rb = g->rebuild != 0u;
-  const double* ax = rb ? sx : px;  // step-start centres: gathered on a rebuild, in place otherwise
-  const double* ay = rb ? sy : py;
-  const double* az = rb ? sz : pz;
-  const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
-  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
-  const float inv = g->invLq;
-  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
-  unsigned md = 0;
-  float dmax = 0.f;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double x0 = ax[i], y0 = ay[i], z0 = az[i];
-    const float Dx = ddx[i], Dy = ddy[i], Dz = ddz[i];
-    const double nx = __dadd_rn(x0, f2d_exact(Dx));
-    const double ny = __dadd_rn(y0, f2d_exact(Dy));
-    const double nz = __dadd_rn(z0, f2d_exact(Dz));
-    px[i] = nx;
-    py[i] = ny;
-    pz[i] = nz;
-    float4 q = p4[i];
-    q.x += Dx;
-    q.y += Dy;
-    q.z += Dz;
-    p4[i] = q;
-    const float D = (rb ? 0.f : disp[i]) + sqrtf(Dx * Dx + Dy * Dy + Dz * Dz);
-    disp[i] = D;
-    dmax = fmaxf(dmax, D);
-    if (!rb) {
-      int ix = box_div(quantise(x0) - O0, Lq, inv);
-      int iy = box_div(quantise(y0) - O1, Lq, inv);
-      int iz = box_div(quantise(z0) - O2, Lq, inv);
-      if (ix >= d0 || iy >= d1 || iz >= d2) {  // impossible by construction of the bounds
-        atomicOr(&g->err, (unsigned)ERR_BOUNDS);
-        ix = min(ix, d0 - 1); iy = min(iy, d1 - 1); iz = min(iz, d2 - 1);
-      }
-      skey[i] = (unsigned)ix + (unsigned)d0 * ((unsigned)iy + (unsigned)d1 * (unsigned)iz);
-    }
-    const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
-    mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
-    mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
-    mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
-    const unsigned dbits = __float_as_uint(2.0f * q.w);
-    md = dbits > md ? dbits : md;
-  }
-  // non-negative floats order like their bits
-  const unsigned wmax = warp_reduce(__float_as_uint(dmax), [](unsigned a, unsigned b) { return a > b ? a : b; });
-  if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_dmax, wmax);
-  block_commit_bounds<kBlock>(mn, mx, md, g);  // contains a __syncthreads
-  if (threadIdx.x == 0 && s_dmax) atomicMax(&g->max_disp, s_dmax);
 }
 
 // Keep one attribute buffer current: a rebuild's gather writes the canonical order into the other.
@@ -1023,28 +1070,24 @@ void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr,
                                                 g, c);
 }
 
-void launch_force_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, MechConsts c, bool build,
-                       int grid_blocks) {
+void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g, MechConsts c,
+                       bool build, int grid_blocks) {
+  const AgentArrays& P = b.pset[cur];
+  const AgentArrays& N = b.pset[cur ^ 1];
   if (build)
-    k_force_skin<true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x,
-                                                   b.pos.y, b.pos.z, b.p4, b.skey, b.start, b.list,
-                                                   b.list_n, b.delta[0], b.delta[1], b.delta[2],
-                                                   b.nbr, g, c);
+    k_force_skin<true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
+                                                   b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
+                                                   b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
+                                                   g, c);
   else
-    k_force_skin<false><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x,
-                                                    b.pos.y, b.pos.z, b.p4, b.skey, b.start, b.list,
-                                                    b.list_n, b.delta[0], b.delta[1], b.delta[2],
-                                                    b.nbr, g, c);
+    k_force_skin<false><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
+                                                    b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
+                                                    b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
+                                                    g, c);
 }
 
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
   k_list_build<<<grid_blocks, kBlock, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
-}
-
-void launch_apply_skin(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
-  k_apply_skin<<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x, b.pos.y,
-                                              b.pos.z, b.p4, b.delta[0], b.delta[1], b.delta[2],
-                                              b.disp, b.skey, g);
 }
 
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
@@ -1052,12 +1095,11 @@ void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays&
   k_attr_copy<<<grid_blocks, kBlock, 0, s>>>(src, dst, g);
 }
 
-int force_skin_blocks_per_sm() {
-  int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_force_skin<true>, kFT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force_skin<false>, kFT, 0);
-  const int m = a < b ? a : b;
-  return m > 0 ? m : 1;
+int force_skin_blocks_per_sm(bool build) {
+  int a = 0;
+  if (build) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_force_skin<true>, kFT, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_force_skin<false>, kFT, 0);
+  return a > 0 ? a : 1;
 }
 
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
