@@ -39,9 +39,9 @@ KERNEL_BYTES = {
     "scatter": lambda B: 12 + 4 + 4 * B,         # key + rank in, starts, perm out
     "gather": lambda B: 44 + 48 + 4 * B,         # perm, key, payload (32) in; payload + skey + p4 out
     "force_mixed": lambda B: 44 + 28 + 4 * B,    # p4, FP64 centre, skey in; centre + count out
-    "force_list": lambda m: 100 + 4 * m,         # list (4 B per entry) + count, own p4, FP64 centre
-                                                 # and move in; centre, p4, move, neighbour count
-                                                 # and read-out box id out (the update is fused)
+    "force_list": lambda m: 96 + 4 * m,          # list (4 B per entry) + count, own p4, FP64 centre
+                                                 # and move in; centre, p4, move and neighbour count
+                                                 # out (the update is fused)
 }
 STEP_BYTES_PER_AGENT = lambda B: 4 * 32 + 8 * B  # rebuild + force + update, agent state S = 32 B
 # Algorithmic FP32 work of the force kernel: 9 FLOP per candidate pair of the 27-box search (3 sub,

@@ -850,6 +850,8 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
     unsigned* onbr = st->neighbour_count ? b.key : nullptr;
     unsigned* obox = st->box_id ? b.rank : nullptr;
     const bool pos = st->x || st->y || st->z;
+    if (obox && b.pset[1].x)  // skin: a list step's box ids come from its step-start centres
+      RUN("readout_box", 1, launch_readout_box(sm, b.pset[s->pos_cur ^ 1], b.skey, s->g, s->blocks_stream));
     RUN("unsort", 1, launch_unsort(sm, b, A, s->g, pos ? b.sorted.x : nullptr, b.sorted.y, b.sorted.z, odiam, ovol,
                                    onbr, obox, s->blocks_stream));
     if (st->x) CK(cudaMemcpyAsync(st->x, b.sorted.x, n * sizeof(double), cudaMemcpyDeviceToHost, sm));

@@ -69,6 +69,7 @@ struct DevGrid {
   unsigned long long list_entries;  // listed candidates of the last rebuild
   float list_L2f;                 // list radius squared (R + skin)^2, widened by 2^-10
   float Lf_list;                  // box length (um) of the grid the lists were built on
+  unsigned n_step;                // agents the last step moved (a list step's box-id read-out)
 };
 
 struct MechConsts {               // per-simulation constants passed by value
@@ -290,6 +291,8 @@ void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int gri
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
                       int grid_blocks);
 int force_skin_blocks_per_sm(bool build);
+void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,
+                        int grid_blocks);
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                  double dv, double vdiv, int grid_blocks);
 void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -94,6 +94,7 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
       __uint_as_float(g->max_disp) <= c.skin_half && g->since_rebuild + 1u < c.max_cadence)
     rebuild = 0u;
   g->rebuild = rebuild;
+  g->n_step = g->nbox ? n : 0u;
   if (rebuild) {
     g->n_sort = g->nbox ? n : 0u;
     g->nbox1_sort = g->nbox1;

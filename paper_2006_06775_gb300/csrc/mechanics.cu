@@ -556,8 +556,8 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     }
     nbr[i] = cnt;
     // update: FP64 centre += displacement (exact conversion, one FP64 add), FP32 offset +=
-    // displacement, move since the rebuild; on a list step also the box of the step-start centre
-    // for the read-out (a rebuild's gather has written it already)
+    // displacement, move since the rebuild (a list step's box ids are derived on read-out:
+    // k_readout_box)
     double x0, y0, z0;
     float dprev = 0.f;
     if constexpr (BUILD) {
@@ -582,18 +582,6 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     const float D = (rb ? 0.f : dprev) + sqrtf(Dx * Dx + Dy * Dy + Dz * Dz);
     disp[i] = D;
     s_dm[t] = fmaxf(s_dm[t], D);
-    if (!BUILD && !rb) {
-      const long long Lq = g->Lq;
-      const float inv = g->invLq;
-      int bx = box_div(quantise(x0) - g->O[0], Lq, inv);
-      int by = box_div(quantise(y0) - g->O[1], Lq, inv);
-      int bz = box_div(quantise(z0) - g->O[2], Lq, inv);
-      if (bx >= d0 || by >= d1 || bz >= d2) {  // impossible by construction of the bounds
-        atomicOr(&g->err, (unsigned)ERR_BOUNDS);
-        bx = min(bx, d0 - 1); by = min(by, d1 - 1); bz = min(bz, d2 - 1);
-      }
-      skey[i] = (unsigned)bx + (unsigned)d0 * ((unsigned)by + (unsigned)d1 * (unsigned)bz);
-    }
     const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
     s_mn[0][t] = e0 < s_mn[0][t] ? e0 : s_mn[0][t];
     s_mx[0][t] = e0 > s_mx[0][t] ? e0 : s_mx[0][t];
@@ -669,6 +657,30 @@ __global__ void __launch_bounds__(kBlock) k_list_build(const float4* __restrict_
   if (overflow) g->list_overflow = 1u;  // this step's forces come from the walk, the next rebuilds
   listed = warp_reduce(listed, [](unsigned a, unsigned b) { return a + b; });
   if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g->list_entries, (unsigned long long)listed);
+}
+
+// Box-id read-out after a list step: the box of each agent's step-start centre on that step's grid
+// (after a rebuild step the gather has written it).  The step-start centres are the position set
+// the step read, the one that is not current after it.  Only agents that took part in the step.
+__global__ void __launch_bounds__(kBlock) k_readout_box(const double* __restrict__ x,
+                                                        const double* __restrict__ y,
+                                                        const double* __restrict__ z,
+                                                        unsigned* __restrict__ skey, DevGrid* g) {
+  if (g->rebuild) return;
+  const unsigned n = g->n_step;
+  const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const float inv = g->invLq;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int bx = box_div(quantise(x[i]) - O0, Lq, inv);
+    int by = box_div(quantise(y[i]) - O1, Lq, inv);
+    int bz = box_div(quantise(z[i]) - O2, Lq, inv);
+    if (bx >= d0 || by >= d1 || bz >= d2) {  // impossible by construction of the bounds
+      atomicOr(&g->err, (unsigned)ERR_BOUNDS);
+      bx = min(bx, d0 - 1); by = min(by, d1 - 1); bz = min(bz, d2 - 1);
+    }
+    skey[i] = (unsigned)bx + (unsigned)d0 * ((unsigned)by + (unsigned)d1 * (unsigned)bz);
+  }
 }
 
 // Keep one attribute buffer current: a rebuild's gather writes the canonical order into the other.
@@ -1088,6 +1100,11 @@ void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g
 
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
   k_list_build<<<grid_blocks, kBlock, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
+}
+
+void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,
+                        int grid_blocks) {
+  k_readout_box<<<grid_blocks, kBlock, 0, s>>>(start_pos.x, start_pos.y, start_pos.z, skey, g);
 }
 
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
