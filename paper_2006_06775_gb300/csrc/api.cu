@@ -125,7 +125,7 @@ struct bdm_sim {
   Profiler prof;
   bool capturing = false;
   unsigned long long capture_kernels = 0;
-  int blocks_stream = 1216, blocks_force = 608, blocks_walk = 608, blocks_scan = 608;
+  int blocks_stream = 1216, blocks_force = 608, blocks_walk = 608, blocks_list = 912, blocks_scan = 608;
   unsigned n_stage = 0;     // host source of the agent-count upload
 };
 
@@ -420,6 +420,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
                                                       : force_mixed_blocks_per_sm(s->mc.force_variant))
                              : force_fp64_blocks(C, s->sms);
   s->blocks_walk = p.skin > 0.0 ? s->sms * force_skin_blocks_per_sm(true) : s->blocks_force;
+  s->blocks_list = s->sms * list_build_blocks_per_sm();
   const size_t tiles = s->is_sir ? s->sb.max_tiles : s->mb.max_tiles;
   s->blocks_scan = (int)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)s->sms * 4));
   s->allocated = true;
@@ -510,7 +511,7 @@ int enqueue_mech_step(bdm_sim* s) {
   RUN("gather", 1, launch_gather(st, b, A, B, g, s->mixed, s->blocks_stream));
   if (s->mc.skin > 0.0) {
     RUN("attr_copy", 1, launch_attr_copy(st, B, A, g, s->blocks_stream));
-    RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_stream));
+    RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_list));
     RUN("force_walk", 1, launch_force_skin(st, b, s->pos_cur, g, s->mc, true, s->blocks_walk));  // overflow only
     RUN("force_list", 1, launch_force_skin(st, b, s->pos_cur, g, s->mc, false, s->blocks_force));
     s->pos_cur ^= 1;  // the force kernels wrote the step's result into the other position set

@@ -291,6 +291,7 @@ void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int gri
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
                       int grid_blocks);
 int force_skin_blocks_per_sm(bool build);
+int list_build_blocks_per_sm();
 void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,
                         int grid_blocks);
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

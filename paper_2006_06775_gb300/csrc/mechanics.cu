@@ -607,52 +607,75 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
 }
 
 // Lists of a rebuild step: the canonical 27-box walk on a grid of box length >= R + skin, keeping
-// every candidate within R + skin (no forces; the list kernel computes them from the lists).
-__global__ void __launch_bounds__(kBlock) k_list_build(const float4* __restrict__ p4,
-                                                       const unsigned* __restrict__ skey,
-                                                       const unsigned* __restrict__ start,
-                                                       unsigned* __restrict__ list,
-                                                       unsigned* __restrict__ list_n, DevGrid* g) {
+// every candidate within R + skin (no forces; the list kernel computes them from the lists).  The
+// nine row runs of an agent (each its boxes x-1, x, x+1, contiguous in the canonical order) are
+// first collected into a per-thread table in shared memory, all 36 run bounds loaded at once; the
+// candidates of all runs are then visited in ONE loop, so a warp's lanes, whose runs differ in
+// length, wait only for the lane with the most candidates in total rather than for the longest run
+// of every row.  Entries are written in the canonical order.
+constexpr int kLB = 256;  // threads per block of the list build
+
+__global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p4,
+                                                    const unsigned* __restrict__ skey,
+                                                    const unsigned* __restrict__ start,
+                                                    unsigned* __restrict__ list,
+                                                    unsigned* __restrict__ list_n, DevGrid* g) {
   if (!g->rebuild) return;
+  // non-empty row runs: (first | row << 27, end of box x-1, end of box x, end of run)
+  __shared__ uint4 s_run[9][kLB];
   const unsigned n = g->nbox ? g->n : 0u;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const float Lf = g->Lf, L2 = g->list_L2f;
+  const int t = threadIdx.x;
   unsigned overflow = 0, listed = 0;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = blockIdx.x * kLB + (unsigned)t; i < n; i += gridDim.x * kLB) {
     const unsigned b = __ldg(skey + i);
     const int ix = (int)(b % (unsigned)d0);
     const unsigned q0 = b / (unsigned)d0;
     const int iy = (int)(q0 % (unsigned)d1), iz = (int)(q0 / (unsigned)d1);
-    const int xl = ix > 0 ? ix - 1 : 0, xh = ix + 1 < d0 ? ix + 1 : ix;
     const float4 pi = __ldg(p4 + i);
-    const float pxm = pi.x + Lf, px0 = pi.x, pxp = pi.x - Lf;
-    unsigned ln = 0;
-#pragma unroll 1
+    unsigned nr = 0;
+#pragma unroll
     for (int sg = 0; sg < 9; ++sg) {
       const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
       if (jz < 0 || jz >= d2 || jy < 0 || jy >= d1) continue;
-      const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
-      const unsigned a = __ldg(start + row + xl);
-      const unsigned m1 = ix > 0 ? __ldg(start + row + ix) : a;
-      const unsigned m2 = __ldg(start + row + ix + 1);
-      const unsigned e = __ldg(start + row + xh + 1);
-      const float py = pi.y - (float)(sg % 3 - 1) * Lf, pz = pi.z - (float)(sg / 3 - 1) * Lf;
-      for (unsigned j = a; j < e; ++j) {
+      const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0 + (unsigned)ix;
+      const unsigned e1 = __ldg(start + row), e2 = __ldg(start + row + 1);
+      const unsigned e0 = ix > 0 ? __ldg(start + row - 1) : e1;
+      const unsigned e3 = ix + 1 < d0 ? __ldg(start + row + 2) : e2;
+      if (e3 > e0) s_run[nr++][t] = make_uint4(e0 | ((unsigned)sg << 27), e1, e2, e3);
+    }
+    unsigned ln = 0;
+    if (nr) {
+      unsigned r = 0;
+      uint4 run = s_run[0][t];
+      unsigned j = run.x & 0x7FFFFFFu, cb = (run.x >> 27) * 3u;
+      float py = pi.y - (float)((int)(run.x >> 27) % 3 - 1) * Lf;
+      float pz = pi.z - (float)((int)(run.x >> 27) / 3 - 1) * Lf;
+      for (;;) {
         const float4 q = __ldg(p4 + j);
-        const unsigned bx = j < m1 ? 0u : (j < m2 ? 1u : 2u);
-        const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
+        const unsigned bx = (j >= run.y ? 1u : 0u) + (j >= run.z ? 1u : 0u);
+        const float ex = (pi.x - (float)((int)bx - 1) * Lf) - q.x;
         const float ey = py - q.y;
         const float ez = pz - q.z;
         const float dd = ex * ex + ey * ey + ez * ez;
         if (dd <= L2 && j != i) {
-          if (ln < kListCap) list[list_at(i, ln)] = (j << 5) | (unsigned)(sg * 3 + (int)bx);
+          if (ln < (unsigned)kListCap) list[list_at(i, ln)] = (j << 5) | (cb + bx);
           ++ln;
+        }
+        if (++j == run.w) {  // next row run
+          if (++r == nr) break;
+          run = s_run[r][t];
+          j = run.x & 0x7FFFFFFu;
+          cb = (run.x >> 27) * 3u;
+          py = pi.y - (float)((int)(run.x >> 27) % 3 - 1) * Lf;
+          pz = pi.z - (float)((int)(run.x >> 27) / 3 - 1) * Lf;
         }
       }
     }
-    list_n[i] = ln < kListCap ? ln : kListCap;
-    overflow |= ln > kListCap ? 1u : 0u;
-    listed += ln < kListCap ? ln : kListCap;
+    list_n[i] = ln < (unsigned)kListCap ? ln : (unsigned)kListCap;
+    overflow |= ln > (unsigned)kListCap ? 1u : 0u;
+    listed += ln < (unsigned)kListCap ? ln : (unsigned)kListCap;
   }
   if (overflow) g->list_overflow = 1u;  // this step's forces come from the walk, the next rebuilds
   listed = warp_reduce(listed, [](unsigned a, unsigned b) { return a + b; });
@@ -1099,7 +1122,7 @@ void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g
 }
 
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
-  k_list_build<<<grid_blocks, kBlock, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
+  k_list_build<<<grid_blocks, kLB, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
 }
 
 void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,
@@ -1110,6 +1133,12 @@ void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* 
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
                       int grid_blocks) {
   k_attr_copy<<<grid_blocks, kBlock, 0, s>>>(src, dst, g);
+}
+
+int list_build_blocks_per_sm() {
+  int a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_list_build, kLB, 0);
+  return a > 0 ? a : 1;
 }
 
 int force_skin_blocks_per_sm(bool build) {
