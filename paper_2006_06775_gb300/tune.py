@@ -25,7 +25,7 @@ import numpy as np
 MECH_CANDIDATES = ([dict(box_factor=1.0, force_variant=0, skin=0.0),
                     dict(box_factor=1.15, force_variant=0, skin=0.0),
                     dict(box_factor=1.0, force_variant=1, skin=0.0)] +
-                   [dict(box_factor=1.0, force_variant=0, skin=s) for s in (1.5, 2.0, 2.5, 3.0)])
+                   [dict(box_factor=1.0, force_variant=0, skin=s) for s in (1.0, 1.5, 2.0, 2.5, 3.0, 3.5)])
 
 
 def workload_signature(params, n, volume):
