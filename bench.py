@@ -327,10 +327,11 @@ def run_ours(args):
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
 
     sim.close()
-    ensemble = serving = plain = spheroid = None
+    ensemble = serving = plain = spheroid = stationary = None
     if rank == 0 and not args.no_small:
         plain = bench_plain()
         spheroid = bench_spheroid()
+        stationary = bench_stationary()
     if rank == 0 and not args.no_ensemble:
         ensemble = bench_ensemble(args.ensemble_steps, args.ensemble_baseline_runs)
     if rank == 0 and args.serve_requests > 0:
@@ -367,7 +368,8 @@ def run_ours(args):
             "kernels_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
             "diffusion": diffusion,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
-            "plain": plain, "spheroid": spheroid, "ensemble": ensemble, "serving": serving,
+            "plain": plain, "spheroid": spheroid, "stationary": stationary, "ensemble": ensemble,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -472,6 +474,34 @@ def fp64_peak_tflops(n=4096, reps=5):
     stream = torch.cuda.current_stream()
     ms = _event_time_ms(stream, lambda: [torch.matmul(a, b) for _ in range(reps)])
     return 2.0 * n ** 3 * reps / (ms * 1e-3) / 1e12
+
+
+def bench_stationary(n=10_000_000, steps=10, warmup=3, skin=2.5):
+    """A settled lattice around a relaxing ball (10% of 10^7 agents), neighbour lists with a 2.5 um
+    skin: steps with stationary agents skipped against the same steps evaluating every agent (the
+    results are identical).  `skipped_per_list_step` is the fraction of agents skipped on a list step."""
+    from paper_2006_06775_gb300 import bdm
+    params, inp = synth.settled_mechanics(n, 0.1)
+    R = float(np.max(inp["diameter"]))
+    params = dict(params, interaction_radius=R, skin=skin)
+    out = {"workload": "settled lattice (spacing 14 um) around a ball of overlapping agents at 0.3 "
+                       "volume fraction holding 10%% of %d agents; skin %.1f um" % (n, skin),
+           "steps": steps, "warmup": warmup}
+    for key, skip in (("skip", 1), ("evaluate_all", 0)):
+        sim = bdm.Sim(dict(params, skip_stationary=skip))
+        sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+        sim.step(warmup)
+        s0 = sim.get_state(fields=())
+        ms = _event_time_ms(sim.stream, lambda: sim.step(steps))
+        s1 = sim.get_state(fields=())
+        sim.close()
+        rebuilds = int(s1["grid_rebuilds"]) - int(s0["grid_rebuilds"])
+        skipped = int(s1["stationary_skipped"]) - int(s0["stationary_skipped"])
+        out[key] = {"ms_per_step": ms / steps, "agent_steps_per_s": n * steps / (ms * 1e-3),
+                    "grid_rebuilds": rebuilds,
+                    "skipped_per_list_step": skipped / max(1, n * (steps - rebuilds))}
+    out["speedup"] = out["evaluate_all"]["ms_per_step"] / out["skip"]["ms_per_step"]
+    return out
 
 
 def bench_spheroid(max_agents=1_000_000, max_steps=160):

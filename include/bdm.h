@@ -105,6 +105,11 @@ typedef struct bdm_params {
   uint64_t capacity;             /* max agents (growth appends up to it); 0 = agents of the first
                                     bdm_add_agents call                                           */
   uint64_t box_capacity;         /* max grid boxes; 0 = automatic (4 x initial + margin)           */
+  /* Stationary agents (skin > 0): on a list step an agent that, with every listed neighbour, kept
+     its position in the previous step would get the same force, displacement (zero) and neighbour
+     count again, so it can be left out.  The results are identical either way. */
+  int32_t skip_stationary;       /* 1 = skip such agents; 0 = evaluate every agent every step     */
+  int32_t reserved4;
   /* Device plumbing. */
   void* stream;                  /* cudaStream_t, NULL = a stream the handle creates              */
   void* (*alloc)(size_t bytes, void* user); /* optional device allocator                         */
@@ -138,6 +143,7 @@ typedef struct bdm_state {
   int64_t grid_box_q;            /* out: box length, lattice units                                 */
   int64_t grid_dims[3];          /* out: boxes per axis                                            */
   uint64_t list_entries;         /* out: listed candidates at the last rebuild (skin > 0)          */
+  uint64_t stationary_skipped;   /* out: agent evaluations skipped as stationary, all steps so far */
 } bdm_state;
 
 typedef struct bdm_sim bdm_sim;

@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("reserved2", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32), ("reserved3", ctypes.c_uint32),
         ("capacity", ctypes.c_uint64), ("box_capacity", ctypes.c_uint64),
+        ("skip_stationary", ctypes.c_int32), ("reserved4", ctypes.c_int32),
         ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
     ]
@@ -55,7 +56,7 @@ class State(ctypes.Structure):
         ("mass_total", ctypes.c_double), ("sir_counts", ctypes.c_uint32 * 3),
         ("grid_rebuilds", ctypes.c_uint32), ("grid_origin_q", ctypes.c_int64 * 3),
         ("grid_box_q", ctypes.c_int64), ("grid_dims", ctypes.c_int64 * 3),
-        ("list_entries", ctypes.c_uint64),
+        ("list_entries", ctypes.c_uint64), ("stationary_skipped", ctypes.c_uint64),
     ]
 
 
@@ -150,7 +151,7 @@ def make_params(d: dict) -> Params:
                  "sir_step", "p_infect", "p_recover"):
         if name in d:
             setattr(p, name, float(d[name]))
-    for name in ("growth_enabled", "force_variant", "diffusion_enabled", "sir_boxes"):
+    for name in ("growth_enabled", "force_variant", "diffusion_enabled", "sir_boxes", "skip_stationary"):
         if name in d:
             setattr(p, name, int(d[name]))
     if "grid_n" in d:
@@ -236,7 +237,7 @@ def bdm_get_state(h, fields=FIELDS, grid_size=0, out=None):
     res = dict(arrays)
     res.update(n=int(st2.n), step=int(st2.step), mass_total=float(st2.mass_total),
                sir_counts=np.array(st2.sir_counts[:], np.uint32), grid_rebuilds=int(st2.grid_rebuilds),
-               list_entries=int(st2.list_entries),
+               list_entries=int(st2.list_entries), stationary_skipped=int(st2.stationary_skipped),
                grid_origin_q=np.array(st2.grid_origin_q[:], np.int64),
                grid_box_q=int(st2.grid_box_q), grid_dims=np.array(st2.grid_dims[:], np.int64))
     return res

@@ -368,6 +368,8 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
           (rc = dalloc_n(s, &b.pset[1].y, C)) || (rc = dalloc_n(s, &b.pset[1].z, C)) ||
           (rc = dalloc_n(s, &b.p4set[1], C)))
         return rc;
+      if (p.skip_stationary && ((rc = dalloc_n(s, &b.moved[0], C)) || (rc = dalloc_n(s, &b.moved[1], C))))
+        return rc;
       CK(cudaMemsetAsync(b.list_n, 0, sizeof(unsigned) * C, s->stream));
       CK(cudaMemsetAsync(b.disp, 0, sizeof(float) * C, s->stream));
     }
@@ -398,6 +400,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     mc.skin = p.skin;
     mc.skin_half = (float)(0.5 * p.skin * (1.0 - 1e-5));
     mc.max_cadence = 64;
+    mc.skip_stationary = p.skip_stationary ? 1 : 0;
   }
   if (s->diffusion) {
     const size_t nv = (size_t)p.grid_n[0] * p.grid_n[1] * p.grid_n[2];
@@ -765,6 +768,7 @@ int bdm_reset(bdm_sim* s) {
   s->gh->sir_sources = 0;
   s->gh->list_valid = 0;
   s->gh->rebuilds = 0;
+  s->gh->skipped = 0;
   CK(cudaMemcpy(s->g, s->gh, sizeof(DevGrid), cudaMemcpyHostToDevice));
   // the SIR box histogram already holds the removed agents for their next step
   if (s->is_sir) CK(cudaMemset(s->sb.count, 0, sizeof(unsigned) * (s->box_capacity + 1)));
@@ -827,6 +831,7 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
   st->grid_box_q = G.Lq;
   st->grid_rebuilds = G.rebuilds;
   st->list_entries = G.list_entries;
+  st->stationary_skipped = G.skipped;
   cudaStream_t sm = s->stream;
   if (s->is_sir) {
     const SirState& S = s->sb.a;

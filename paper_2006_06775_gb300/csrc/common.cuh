@@ -70,6 +70,7 @@ struct DevGrid {
   float list_L2f;                 // list radius squared (R + skin)^2, widened by 2^-10
   float Lf_list;                  // box length (um) of the grid the lists were built on
   unsigned n_step;                // agents the last step moved (a list step's box-id read-out)
+  unsigned long long skipped;     // agent evaluations skipped as stationary (list steps)
 };
 
 struct MechConsts {               // per-simulation constants passed by value
@@ -81,6 +82,7 @@ struct MechConsts {               // per-simulation constants passed by value
   double skin;                    // neighbour-list skin (um); 0: grid walk every step
   float skin_half;                // rebuild when an agent may have moved more than this
   unsigned max_cadence;           // rebuild at least every this many steps (bounds FP32 drift)
+  int skip_stationary;            // list steps skip agents that, with their listed neighbours, stood still
 };
 
 // ---- exact helpers -------------------------------------------------------------------------
@@ -263,6 +265,7 @@ struct MechBuffers {
   unsigned* list;
   unsigned* list_n;
   float* disp;                   // |moves| of each agent since the last rebuild
+  unsigned char* moved[2];       // 1 if the agent's displacement was nonzero (alternate like pset)
 };
 
 // grid.cu

@@ -346,14 +346,15 @@ __device__ __noinline__ unsigned list_rescan(unsigned i, unsigned m, const unsig
 // values while each agent's own update is written at once (no separate update pass).  On a rebuild
 // step the centres come from the gather's set and the offsets from the current set's offset buffer,
 // which the gather has overwritten in canonical order.
-template <bool BUILD>
+template <bool BUILD, bool SKIP = false>
 __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     const double* __restrict__ gx, const double* __restrict__ gy, const double* __restrict__ gz,
     const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pz,
     const float4* __restrict__ p4, double* __restrict__ ox, double* __restrict__ oy,
     double* __restrict__ oz, float4* __restrict__ op4, unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, unsigned* __restrict__ list, unsigned* __restrict__ list_n,
-    float* __restrict__ disp, unsigned* __restrict__ nbr, DevGrid* g, MechConsts c) {
+    float* __restrict__ disp, unsigned* __restrict__ nbr, const unsigned char* __restrict__ mprev,
+    unsigned char* __restrict__ mnext, DevGrid* g, MechConsts c) {
   // BUILD: the walk with forces, only on a rebuild step whose lists overflowed; otherwise the lists
   // (built by k_list_build on a rebuild step) give the forces
   if (BUILD ? !(g->rebuild && g->list_overflow) : g->list_overflow != 0u) return;
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   __shared__ unsigned long long s_mn[3][kFT], s_mx[3][kFT];
   __shared__ unsigned s_md[kFT];
   __shared__ float s_dm[kFT];
+  __shared__ unsigned s_skip;  // agents of the block skipped as stationary
   // list steps: the next agent's offsets, list length and first four entries are copied ahead
   // (double-buffered), and this agent's FP64 centre and move arrive during its force loop
   __shared__ float4 s_pi[2][kFT];
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   }
   s_md[t] = 0u;
   s_dm[t] = 0.f;
+  if (t == 0) s_skip = 0u;
   __syncthreads();
   const unsigned stride = gridDim.x * blockDim.x;
   auto prefetch = [&](unsigned a, int b) {  // list step: agent a's offsets, list length, entries 0-3
@@ -405,12 +408,16 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   };
   unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   int buf = 0;
+  // stationary agents are looked for only on list steps (a rebuild renumbers the agents)
+  const bool look = SKIP && !BUILD && !rb;
   if constexpr (!BUILD) {
     if (i < n) prefetch(i, 0);
     cp_async_commit();
   }
   for (; i < n; i += stride) {
     float4 pi;
+    bool still = false;
+    const bool own_still = look && __ldg(mprev + i) == 0;
     if constexpr (BUILD) {
       pi = __ldg(p4 + i);
     } else {
@@ -504,7 +511,18 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     } else {
       // four entries at a time, their loads and their candidates' loads issued together, so the loop
       // does not wait on one dependent load pair per entry
-      const unsigned m = s_m[buf][t];
+      // stationary: this agent and every listed neighbour kept their position in the previous step,
+      // so the evaluation would repeat (zero displacement, the same count): it is skipped
+      if (SKIP && own_still) {
+        const unsigned ml = s_m[buf][t];
+        still = true;
+        for (unsigned k = 0; k < ml && still; ++k) {
+          const unsigned v = k < 4u ? s_v[buf][k][t] : __ldg(list + list_at(i, k));
+          still = __ldg(mprev + (v >> 5)) == 0;
+        }
+        if (still) atomicAdd(&s_skip, 1u);
+      }
+      const unsigned m = still ? 0u : s_m[buf][t];
       for (unsigned k0 = 0; k0 < m; k0 += 4) {
         unsigned v[4];
         if (k0 == 0) {
@@ -554,7 +572,8 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
       const float f = c.capf * rsqrtf(n2);
       Dx *= f; Dy *= f; Dz *= f;
     }
-    nbr[i] = cnt;
+    if (!still) nbr[i] = cnt;  // a skipped agent keeps the previous step's count
+    if (mnext) mnext[i] = (Dx != 0.f || Dy != 0.f || Dz != 0.f) ? 1 : 0;
     // update: FP64 centre += displacement (exact conversion, one FP64 add), FP32 offset +=
     // displacement, move since the rebuild (a list step's box ids are derived on read-out:
     // k_readout_box)
@@ -604,6 +623,9 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   unsigned long long mx[3] = {s_mx[0][t], s_mx[1][t], s_mx[2][t]};
   block_commit_bounds<kFT>(mn, mx, s_md[t], g);  // contains a __syncthreads
   if (t == 0 && s_dmax) atomicMax(&g->max_disp, s_dmax);
+  if constexpr (SKIP && !BUILD) {  // s_skip is final: block_commit_bounds has synchronised the block
+    if (t == 0 && s_skip) atomicAdd(&g->skipped, (unsigned long long)s_skip);
+  }
 }
 
 // Lists of a rebuild step: the canonical 27-box walk on a grid of box length >= R + skin, keeping
@@ -1113,12 +1135,18 @@ void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g
     k_force_skin<true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
                                                    b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
                                                    b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
-                                                   g, c);
+                                                   b.moved[cur], b.moved[cur ^ 1], g, c);
+  else if (c.skip_stationary)
+    k_force_skin<false, true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y,
+                                                          P.z, b.p4set[cur], N.x, N.y, N.z,
+                                                          b.p4set[cur ^ 1], b.skey, b.start, b.list,
+                                                          b.list_n, b.disp, b.nbr, b.moved[cur],
+                                                          b.moved[cur ^ 1], g, c);
   else
     k_force_skin<false><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
                                                     b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
                                                     b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
-                                                    g, c);
+                                                    nullptr, nullptr, g, c);
 }
 
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {

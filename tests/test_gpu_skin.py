@@ -139,3 +139,34 @@ def test_skin_with_secretion_and_diffusion_conserves_mass():
     for _ in range(10):
         mass = (1.0 - 0.01) * (mass + 1.0 * n)
     assert abs(st["mass_total"] - mass) <= 1e-6 * mass
+
+
+def test_stationary_skip_gives_identical_states():
+    """Skipping stationary agents (an agent that, with every listed neighbour, kept its position last
+    step) leaves every result bit-identical, and it does skip on a settled lattice."""
+    params, inp = synth.settled_mechanics(60_000, 0.2)
+    params = dict(params, interaction_radius=R, box_length=R + 2.5, skin=2.5)
+    runs = []
+    for skip in (1, 0):
+        sim = bdm.Sim(dict(params, skip_stationary=skip))
+        sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+        states = []
+        for _ in range(5):
+            sim.step(6)
+            states.append(sim.get_state())
+        runs.append(states)
+        sim.close()
+    for a, b in zip(*runs):
+        for f in ("x", "y", "z", "neighbour_count", "box_id"):
+            assert np.array_equal(a[f], b[f]), f
+    assert runs[1][-1]["stationary_skipped"] == 0
+    lattice = 60_000 - inp["n_active"]
+    assert runs[0][-1]["stationary_skipped"] > lattice
+    assert runs[0][-1]["grid_rebuilds"] < 30
+
+
+def test_stationary_skip_matches_oracle_every_step():
+    params, inp = synth.settled_mechanics(40_000, 0.2, seed=6)
+    params = dict(params, interaction_radius=R, box_length=R + 2.5, skin=2.5, skip_stationary=1)
+    worst, rebuilds = run_teacher_forced(params, inp, 10)
+    assert worst < 2e-5, worst

@@ -165,3 +165,20 @@ def test_all_agents_in_one_box():
     assert np.all(r["neighbour_count"] == 63)
     F = r["force"]
     assert np.all(np.abs(F.sum(axis=0)) <= 1e-12 * np.abs(F).sum())
+
+
+def test_settled_lattice_agents_do_not_move():
+    """The settled workload's premise: lattice agents (no contact within the largest diameter) get
+    exactly zero displacement from the oracle, while the packed ball moves."""
+    params, inp = synth.settled_mechanics(3000, 0.2, seed=7)
+    x, y, z, d = inp["x"], inp["y"], inp["z"], inp["diameter"]
+    out = oracle.mech_step(x, y, z, d, params["dt"], params["repulsion"], params["attraction"],
+                           params["max_displacement"], 12.0, 0.0)
+    moved = (out["x"] != x) | (out["y"] != y) | (out["z"] != z)
+    na = inp["n_active"]
+    r = np.sqrt(x ** 2 + y ** 2 + z ** 2)
+    far = np.arange(len(x)) >= na
+    far &= r > inp["ball_radius"] + 2 * 14.0
+    assert far.sum() > 1000
+    assert not moved[far].any()
+    assert moved[:na].mean() > 0.5
