@@ -9,16 +9,16 @@
 namespace bdm {
 
 // ---------------------------------------------------------------------------------------------
-// Force + capped update, FP64 check path: one thread per agent in canonical order.  Neighbours are
-// read box by box in ascending key -- for each (dz, dy) the up-to-three boxes along x are
-// contiguous in the sorted arrays -- which is exactly the oracle's (box, id) summation order.  Every
-// operation is an explicitly rounded FP64 intrinsic in the oracle's order (no contraction), so
-// positions can match the FP64 oracle bit for bit.  The epilogue folds the new centres into the
-// bounds of the next step's grid.
+// Force + capped update, FP64 check path: one warp per agent in canonical order.  The agent's
+// candidates are read box by box in ascending key -- for each (dz, dy) the up-to-three boxes along x
+// are contiguous in the sorted arrays -- which is exactly the oracle's (box, id) order.  The lanes
+// take the candidates 32 at a time and each evaluates one pair with explicitly rounded FP64
+// intrinsics in the oracle's order (no contraction); the pair forces are then added in candidate
+// order, one after another, by every lane (shuffles), so the sum is the oracle's bit for bit while
+// the long FP64 division and square-root chains of different pairs run side by side.  The epilogue
+// folds the new centres into the bounds of the next step's grid.
 // ---------------------------------------------------------------------------------------------
-// One warp per block: at the small populations this check path is used on, the agents spread over
-// as many SMs as possible (each thread is a long chain of FP64 divisions and square roots).
-constexpr int kF64 = 32;
+constexpr int kF64 = 128;  // threads per block: four agents at a time
 
 __global__ void __launch_bounds__(kF64) k_force_fp64(
     const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
@@ -28,65 +28,99 @@ __global__ void __launch_bounds__(kF64) k_force_fp64(
   const unsigned n = g->nbox ? g->n : 0u;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const double R2 = g->R2;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned warps = gridDim.x * (blockDim.x >> 5);
   unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
   unsigned md = 0;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     const unsigned b = skey[i];
     const int ix = (int)(b % (unsigned)d0);
     const unsigned t = b / (unsigned)d0;
     const int iy = (int)(t % (unsigned)d1), iz = (int)(t / (unsigned)d1);
     const double xi = sx[i], yi = sy[i], zi = sz[i];
     const double ri = 0.5 * (double)diam[i];
-    unsigned cnt = 0;
-    double Sx = 0.0, Sy = 0.0, Sz = 0.0;
-    const int xlo = ix > 0 ? ix - 1 : 0, xhi = ix < d0 - 1 ? ix + 1 : d0 - 1;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int jz = iz + dz;
-      if (jz < 0 || jz >= d2) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int jy = iy + dy;
-        if (jy < 0 || jy >= d1) continue;
+    // row runs: lane r < 9 holds row r's candidate range [ra, ra + len)
+    unsigned ra = 0, len = 0;
+    if (lane < 9u) {
+      const int jz = iz + (int)lane / 3 - 1, jy = iy + (int)lane % 3 - 1;
+      if (jz >= 0 && jz < d2 && jy >= 0 && jy < d1) {
         const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0;
-        const unsigned s0 = start[row + xlo], s1 = start[row + xhi + 1];
-        for (unsigned j = s0; j < s1; ++j) {
-          if (j == i) continue;
-          const double ax = __dsub_rn(xi, sx[j]), ay = __dsub_rn(yi, sy[j]), az = __dsub_rn(zi, sz[j]);
-          const double e2 =
-              __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
-          if (e2 < R2) ++cnt;
-          const double d = __dsqrt_rn(e2);
-          const double rj = 0.5 * (double)diam[j];
-          const double delta = __dsub_rn(__dadd_rn(ri, rj), d);
-          if (delta > 0.0 && d > 0.0) {
-            const double rho = __ddiv_rn(__dmul_rn(ri, rj), __dadd_rn(ri, rj));
-            const double F = __dsub_rn(__dmul_rn(c.k, delta),
-                                       __dmul_rn(c.gamma, __dsqrt_rn(__dmul_rn(rho, delta))));
-            const double s = __ddiv_rn(F, d);
-            Sx = __dadd_rn(Sx, __dmul_rn(s, ax));
-            Sy = __dadd_rn(Sy, __dmul_rn(s, ay));
-            Sz = __dadd_rn(Sz, __dmul_rn(s, az));
-          }
-        }
+        const int xlo = ix > 0 ? ix - 1 : 0, xhi = ix < d0 - 1 ? ix + 1 : d0 - 1;
+        ra = start[row + xlo];
+        len = start[row + xhi + 1] - ra;
       }
     }
-    double Dx = __dmul_rn(c.dt, Sx), Dy = __dmul_rn(c.dt, Sy), Dz = __dmul_rn(c.dt, Sz);
-    double nrm = __dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy));
-    nrm = __dsqrt_rn(__dadd_rn(nrm, __dmul_rn(Dz, Dz)));
-    if (nrm > c.cap) {
-      const double f = __ddiv_rn(c.cap, nrm);
-      Dx = __dmul_rn(Dx, f); Dy = __dmul_rn(Dy, f); Dz = __dmul_rn(Dz, f);
+    unsigned incl = len;  // inclusive scan of the run lengths over lanes 0..8
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += v;
     }
-    const double nx = __dadd_rn(xi, Dx), ny = __dadd_rn(yi, Dy), nz = __dadd_rn(zi, Dz);
-    ox[i] = nx;
-    oy[i] = ny;
-    oz[i] = nz;
-    nbr[i] = cnt;
-    const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
-    mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
-    mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
-    mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
-    const unsigned dbits = __float_as_uint(diam[i]);
-    md = dbits > md ? dbits : md;
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 8);
+    unsigned cnt = 0;
+    double Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    for (unsigned c0 = 0; c0 < total; c0 += 32u) {
+      const unsigned ci = c0 + lane;
+      // the run holding candidate ci, and its index j
+      unsigned j = 0;
+      for (int r = 0; r < 9; ++r) {
+        const unsigned e = __shfl_sync(0xFFFFFFFFu, incl, r);
+        const unsigned a = __shfl_sync(0xFFFFFFFFu, ra, r);
+        const unsigned l = __shfl_sync(0xFFFFFFFFu, len, r);
+        if (ci < e && ci >= e - l) j = a + (ci - (e - l));
+      }
+      bool within = false, contact = false;
+      double fx = 0.0, fy = 0.0, fz = 0.0;
+      if (ci < total && j != i) {
+        const double ax = __dsub_rn(xi, sx[j]), ay = __dsub_rn(yi, sy[j]), az = __dsub_rn(zi, sz[j]);
+        const double e2 =
+            __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+        within = e2 < R2;
+        const double d = __dsqrt_rn(e2);
+        const double rj = 0.5 * (double)diam[j];
+        const double delta = __dsub_rn(__dadd_rn(ri, rj), d);
+        if (delta > 0.0 && d > 0.0) {
+          const double rho = __ddiv_rn(__dmul_rn(ri, rj), __dadd_rn(ri, rj));
+          const double F = __dsub_rn(__dmul_rn(c.k, delta),
+                                     __dmul_rn(c.gamma, __dsqrt_rn(__dmul_rn(rho, delta))));
+          const double sc = __ddiv_rn(F, d);
+          fx = __dmul_rn(sc, ax);
+          fy = __dmul_rn(sc, ay);
+          fz = __dmul_rn(sc, az);
+          contact = true;
+        }
+      }
+      cnt += (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, within));
+      // the contacts' forces added in candidate order
+      unsigned cm = __ballot_sync(0xFFFFFFFFu, contact);
+      while (cm) {
+        const int l = __ffs(cm) - 1;
+        cm &= cm - 1u;
+        Sx = __dadd_rn(Sx, __shfl_sync(0xFFFFFFFFu, fx, l));
+        Sy = __dadd_rn(Sy, __shfl_sync(0xFFFFFFFFu, fy, l));
+        Sz = __dadd_rn(Sz, __shfl_sync(0xFFFFFFFFu, fz, l));
+      }
+    }
+    if (lane == 0u) {
+      double Dx = __dmul_rn(c.dt, Sx), Dy = __dmul_rn(c.dt, Sy), Dz = __dmul_rn(c.dt, Sz);
+      double nrm = __dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy));
+      nrm = __dsqrt_rn(__dadd_rn(nrm, __dmul_rn(Dz, Dz)));
+      if (nrm > c.cap) {
+        const double f = __ddiv_rn(c.cap, nrm);
+        Dx = __dmul_rn(Dx, f); Dy = __dmul_rn(Dy, f); Dz = __dmul_rn(Dz, f);
+      }
+      const double nx = __dadd_rn(xi, Dx), ny = __dadd_rn(yi, Dy), nz = __dadd_rn(zi, Dz);
+      ox[i] = nx;
+      oy[i] = ny;
+      oz[i] = nz;
+      nbr[i] = cnt;
+      const unsigned long long e0 = enc_double(nx), e1 = enc_double(ny), e2 = enc_double(nz);
+      mn[0] = e0 < mn[0] ? e0 : mn[0]; mx[0] = e0 > mx[0] ? e0 : mx[0];
+      mn[1] = e1 < mn[1] ? e1 : mn[1]; mx[1] = e1 > mx[1] ? e1 : mx[1];
+      mn[2] = e2 < mn[2] ? e2 : mn[2]; mx[2] = e2 > mx[2] ? e2 : mx[2];
+      const unsigned dbits = __float_as_uint(diam[i]);
+      md = dbits > md ? dbits : md;
+    }
   }
   block_commit_bounds<kF64>(mn, mx, md, g);
 }
@@ -941,7 +975,7 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed_pairs(
 }
 
 int force_fp64_blocks(size_t capacity, int sms) {
-  const size_t need = (capacity + kF64 - 1) / kF64;
+  const size_t need = (capacity + kF64 / 32 - 1) / (kF64 / 32);  // one warp per agent
   const size_t cap = (size_t)sms * 16;
   return (int)(need < 1 ? 1 : (need < cap ? need : cap));
 }
