@@ -217,6 +217,11 @@ typedef struct bdm_batch_options {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
   void* alloc_user;
+  uint32_t persistent_only;      /* 1 = always the persistent grid kernel; 0 = one CTA per run
+                                    (histogram, scan and counts in shared memory) whenever every
+                                    run's nb^3 + 1 + agents words fit in a CTA's shared memory.
+                                    Both give the same results.                                   */
+  uint32_t reserved0;
 } bdm_batch_options;
 
 /* per_sim: `count` parameter blocks with kind = BDM_SIR (their seed/run_id key each run's Philox
@@ -227,7 +232,8 @@ int bdm_batch_create(const bdm_params* per_sim, int count, const bdm_batch_optio
  * step (the layout is fixed then). */
 int bdm_batch_add_agents(bdm_batch* b, int sim, size_t n, const double* x, const double* y,
                          const double* z, const uint8_t* sir_state);
-/* Advance every run by n steps (asynchronous). */
+/* Advance every run by n steps (asynchronous).  A step is one launch per step: one CTA per run
+ * when the runs fit in shared memory (see persistent_only), else one persistent grid over all runs. */
 int bdm_batch_step(bdm_batch* b, int n);
 /* Wait for the batch's stream; BDM_ETIMEOUT if a grid-barrier wait ran out. */
 int bdm_batch_sync(bdm_batch* b);

@@ -69,7 +69,8 @@ class BatchOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("history_steps", ctypes.c_uint32),
                 ("spin_limit", ctypes.c_uint32), ("barrier_extra", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p)]
+                ("alloc_user", ctypes.c_void_p), ("persistent_only", ctypes.c_uint32),
+                ("reserved0", ctypes.c_uint32)]
 
 
 _lib = None
@@ -359,7 +360,7 @@ class Batch:
     """Batched SIR ensemble: one persistent launch per step for every run; memory from PyTorch."""
 
     def __init__(self, param_dicts, history_steps=0, spin_limit=0, barrier_extra=0, stream=None,
-                 torch_memory=True):
+                 torch_memory=True, persistent_only=False):
         import torch
         self.runs = len(param_dicts)
         self.stream = stream if stream is not None else torch.cuda.Stream()
@@ -368,6 +369,7 @@ class Batch:
         opt.history_steps = int(history_steps)
         opt.spin_limit = int(spin_limit)
         opt.barrier_extra = int(barrier_extra)
+        opt.persistent_only = 1 if persistent_only else 0
         opt.stream = self.stream.cuda_stream
         self._allocator = None
         if torch_memory:

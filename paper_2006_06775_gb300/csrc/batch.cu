@@ -3,11 +3,12 @@
 //
 // The runs keep their own parameters (BioDynaMo, arXiv 2006.06775, Sec. "Epidemiology use case":
 // infection radius and probability, recovery probability, movement bound) and their own agents, in
-// concatenated arrays with per-run offsets.  A work list of (run, 256-agent tile) pairs lets one
-// persistent grid cover every run; its phases (scan of the box histogram, box order and infected
-// list, push of infected agents into their neighbours' counts, update with the next histogram) are
-// separated by a grid barrier whose waits are bounded.  Every run computes exactly what it would
-// compute alone: the arithmetic is integer and per run.
+// concatenated arrays with per-run offsets.  When every run's boxes and counts fit in a CTA's shared
+// memory, a step is one CTA per run whose phases (histogram, scan, box order and infected list, push
+// of infected agents into their neighbours' counts, update) are separated by __syncthreads.
+// Otherwise a work list of (run, 256-agent tile) pairs lets one persistent grid cover every run, its
+// phases separated by a grid barrier whose waits are bounded.  Every run computes exactly what it
+// would compute alone: the arithmetic is integer and per run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +39,8 @@ struct bdm_batch {
   bool cooperative = true;
   unsigned spin_limit = kSpinLimit;
   unsigned barrier_extra = 0;  // test hook: arrivals the grid barrier waits for beyond the grid
+  bool persistent_only = false;
+  size_t runs_smem = 0;        // > 0: one CTA per run with this much dynamic shared memory
   unsigned hist_len = 1024;
   std::vector<void*> allocs;
   std::vector<SirRun> runs;
@@ -188,6 +191,15 @@ int build(bdm_batch* b) {
   const int per_sm = sir_ensemble_blocks_per_sm();
   if (per_sm < 1) return bfail(b, BDM_ECUDA, "persistent SIR kernel cannot be resident");
   b->blocks = sms * per_sm;
+  // one CTA per run when every run's boxes and counts fit in a CTA's shared memory (the grid-barrier
+  // test hook needs the persistent kernel)
+  if (!b->persistent_only && b->barrier_extra == 0) {
+    size_t words = 0;
+    for (const SirRun& r : b->runs)
+      words = std::max(words, (size_t)r.nb * r.nb * r.nb + 1 + r.agent_n);
+    b->runs_smem = sir_runs_smem_bytes(words);
+    cudaGetLastError();
+  }
   // boxes, ranks and histogram of the first step
   launch_sir_init_batch(s, D, b->blocks);
   BCK(cudaGetLastError());
@@ -198,6 +210,12 @@ int build(bdm_batch* b) {
 }
 
 int enqueue(bdm_batch* b, int n) {
+  if (b->runs_smem) {
+    for (int i = 0; i < n; ++i) launch_sir_runs(b->stream, b->dev, b->g, b->runs_smem);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, BDM_ECUDA, "per-run SIR launch failed: %s", cudaGetErrorString(e));
+    return BDM_OK;
+  }
   for (int i = 0; i < n; ++i) {
     cudaError_t e = launch_sir_ensemble(b->stream, b->dev, b->g, b->blocks, b->barrier_extra,
                                         b->spin_limit, b->cooperative);
@@ -247,6 +265,7 @@ int bdm_batch_create(const bdm_params* per_sim, int count, const bdm_batch_optio
     if (opt->history_steps > 0) b->hist_len = (unsigned)opt->history_steps;
     if (opt->spin_limit > 0) b->spin_limit = opt->spin_limit;
     b->barrier_extra = opt->barrier_extra;
+    b->persistent_only = opt->persistent_only != 0;
     b->alloc = opt->alloc;
     b->free = opt->free;
     b->alloc_user = opt->alloc_user;
@@ -311,14 +330,14 @@ int bdm_batch_step(bdm_batch* b, int n) {
       cudaGetLastError();
       rc = enqueue(b, n);
       if (rc) return rc;
-      bdm_count_launches((unsigned long long)n);
+      bdm_count_launches((unsigned long long)n * (b->runs_smem ? 2u : 1u));
       b->steps_done += (unsigned long long)n;
       return BDM_OK;
     }
     it = b->graphs.emplace(n, exec).first;
   }
   BCK(cudaGraphLaunch(it->second, b->stream));
-  bdm_count_launches((unsigned long long)n);
+  bdm_count_launches((unsigned long long)n * (b->runs_smem ? 2u : 1u));
   b->steps_done += (unsigned long long)n;
   return BDM_OK;
 }

@@ -137,17 +137,13 @@ __device__ __forceinline__ void sir_push(unsigned j, const SirRun& r, const SirS
     }
 }
 
-// update phase for agent p of run r: draws, move, read-outs, next box / rank / histogram entry.
-__device__ __forceinline__ unsigned char sir_update(unsigned p, const SirRun& r, SirState a,
-                                                    const unsigned* __restrict__ ninf,
-                                                    unsigned* __restrict__ box,
-                                                    unsigned* __restrict__ kn,
-                                                    unsigned* __restrict__ rk,
-                                                    unsigned* __restrict__ count, unsigned step) {
+// Infection, recovery and move of agent p of run r from its infected-neighbour count `cnt`; writes
+// the new position and state in place and returns the state.
+__device__ __forceinline__ unsigned char sir_advance(unsigned p, const SirRun& r, SirState a,
+                                                     unsigned cnt, unsigned step, int NP[3]) {
   const int P[3] = {a.X[p], a.Y[p], a.Z[p]};
   const unsigned char si = a.st[p];
   const unsigned id = p - r.agent_off;
-  const unsigned cnt = ninf[p];
   unsigned char ns = si;
   if ((si == 0 && cnt > 0) || si == 1) {  // the only cases in which this draw decides anything
     const uint4 w = philox10(make_uint4(id, step, 0u, 0u), r.key);
@@ -157,7 +153,6 @@ __device__ __forceinline__ unsigned char sir_update(unsigned p, const SirRun& r,
   const uint4 mv = philox10(make_uint4(id, step, 1u, 0u), r.key);
   const unsigned W[3] = {mv.x, mv.y, mv.z};
   const long long L = r.L;
-  int NP[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     long long v = (long long)P[k] + ((long long)(((unsigned long long)W[k] * r.span) >> 32) - r.s);
@@ -169,6 +164,18 @@ __device__ __forceinline__ unsigned char sir_update(unsigned p, const SirRun& r,
   a.Y[p] = NP[1];
   a.Z[p] = NP[2];
   a.st[p] = ns;
+  return ns;
+}
+
+// update phase for agent p of run r: draws, move, read-outs, next box / rank / histogram entry.
+__device__ __forceinline__ unsigned char sir_update(unsigned p, const SirRun& r, SirState a,
+                                                    const unsigned* __restrict__ ninf,
+                                                    unsigned* __restrict__ box,
+                                                    unsigned* __restrict__ kn,
+                                                    unsigned* __restrict__ rk,
+                                                    unsigned* __restrict__ count, unsigned step) {
+  int NP[3];
+  const unsigned char ns = sir_advance(p, r, a, ninf[p], step, NP);
   box[p] = kn[p];
   const unsigned b2 = r.box_off + sir_box(NP[0], NP[1], NP[2], r);
   kn[p] = b2;
@@ -340,6 +347,143 @@ __global__ void __launch_bounds__(kBlock) k_sir_ensemble(SirBatchDev B, DevGrid*
   }
 }
 
+// ---- batch of runs, one CTA per run -------------------------------------------------------------
+// When every run's box array and infected-neighbour counts fit in shared memory ((nb^3 + 1 + agents)
+// words), each run is advanced by one CTA per step: histogram, scan and counts live in shared memory,
+// the phases are separated by __syncthreads, and there is neither a grid barrier nor a global scan.
+// Same phases and the same integer arithmetic as the persistent kernel, so the same results (the
+// order of agents inside a box and of the pushes does not enter any result).
+constexpr int kSR = 1024;
+
+// Exclusive prefix sum of v[0..m) in place; every thread of the block calls (v in shared memory).
+__device__ void block_exclusive_scan(unsigned* v, unsigned m) {
+  __shared__ unsigned s_w[kSR / 32];
+  const unsigned t = threadIdx.x, lane = t & 31u, w = t >> 5;
+  const unsigned per = (m + kSR - 1u) / kSR;
+  const unsigned lo = min(t * per, m), hi = min(lo + per, m);
+  unsigned sum = 0;
+  for (unsigned k = lo; k < hi; ++k) sum += v[k];
+  unsigned incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  if (lane == 31u) s_w[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned x = s_w[lane];
+    unsigned xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+      if ((int)lane >= o) xi += y;
+    }
+    s_w[lane] = xi - x;
+  }
+  __syncthreads();
+  unsigned acc = s_w[w] + incl - sum;
+  for (unsigned k = lo; k < hi; ++k) {
+    const unsigned x = v[k];
+    v[k] = acc;
+    acc += x;
+  }
+  __syncthreads();
+}
+
+// push of infected agent j of run r over the run-local box starts and counts in shared memory.
+__device__ __forceinline__ void sir_push_local(unsigned j, const SirRun& r, const SirState a,
+                                               const unsigned* s_start,
+                                               const unsigned* __restrict__ perm, unsigned off,
+                                               unsigned* s_cnt) {
+  const int Xj = a.X[j], Yj = a.Y[j], Zj = a.Z[j];
+  const long long L = r.L;
+  const int nb = r.nb;
+  int cy[3], cz[3], xlo[2], xhi[2];
+  const int ny = neighbour_boxes(box_coord(Yj, r), nb, cy);
+  const int nz = neighbour_boxes(box_coord(Zj, r), nb, cz);
+  const int nr = neighbour_runs(box_coord(Xj, r), nb, xlo, xhi);
+  for (int qz = 0; qz < nz; ++qz)
+    for (int qy = 0; qy < ny; ++qy) {
+      const unsigned row = (unsigned)nb * ((unsigned)cy[qy] + (unsigned)nb * (unsigned)cz[qz]);
+      for (int k = 0; k < nr; ++k) {
+        const unsigned m1 = s_start[row + (unsigned)xhi[k]];
+        for (unsigned m = s_start[row + (unsigned)xlo[k]]; m < m1; ++m) {
+          const unsigned i = perm[off + m];
+          if (i == j) continue;
+          const long long dx = min_image((long long)a.X[i] - Xj, L);
+          const long long dy = min_image((long long)a.Y[i] - Yj, L);
+          const long long dz = min_image((long long)a.Z[i] - Zj, L);
+          if (dx * dx + dy * dy + dz * dz < r.r2) atomicAdd(&s_cnt[i - off], 1u);
+        }
+      }
+    }
+}
+
+__global__ void __launch_bounds__(kSR) k_sir_runs(SirBatchDev B, DevGrid* g) {
+  extern __shared__ unsigned s_dyn[];
+  __shared__ unsigned s_nsrc, s_c[3];
+  const unsigned ri = blockIdx.x;
+  const SirRun r = B.run[ri];
+  const unsigned n = r.agent_n, off = r.agent_off;
+  const unsigned nbox = (unsigned)r.nb * (unsigned)r.nb * (unsigned)r.nb;
+  unsigned* s_box = s_dyn;              // histogram, then box starts (nbox + 1)
+  unsigned* s_cnt = s_dyn + nbox + 1u;  // infected neighbours of each agent of the run
+  const unsigned t = threadIdx.x;
+  const unsigned step = (unsigned)g->step;  // advanced by a separate launch after this one
+  for (unsigned k = t; k <= nbox; k += kSR) s_box[k] = 0u;
+  if (t == 0) {
+    s_nsrc = 0u;
+    s_c[0] = s_c[1] = s_c[2] = 0u;
+  }
+  __syncthreads();
+  // boxes of the step-start positions (also the read-out) and ranks inside them
+  for (unsigned q = t; q < n; q += kSR) {
+    const unsigned p = off + q;
+    const unsigned b = sir_box(B.a.X[p], B.a.Y[p], B.a.Z[p], r);
+    B.kn[p] = b;
+    B.rk[p] = atomicAdd(&s_box[b], 1u);
+    B.box[p] = r.box_off + b;
+    s_cnt[q] = 0u;
+  }
+  __syncthreads();
+  block_exclusive_scan(s_box, nbox + 1u);
+  // box order; infected agents to the source list
+  for (unsigned q = t; q < n; q += kSR) {
+    const unsigned p = off + q;
+    B.perm[off + s_box[B.kn[p]] + B.rk[p]] = p;
+    if (B.a.st[p] == 1) B.src[off + atomicAdd(&s_nsrc, 1u)] = make_uint2(p, ri);
+  }
+  __syncthreads();
+  // infected agents push into their neighbours' counts
+  const unsigned ns = s_nsrc;
+  for (unsigned k = t; k < ns; k += kSR) sir_push_local(B.src[off + k].x, r, B.a, s_box, B.perm, off, s_cnt);
+  __syncthreads();
+  // infection, recovery, move; S/I/R counts of this step
+  unsigned c0 = 0u, c1 = 0u, c2 = 0u;
+  for (unsigned q = t; q < n; q += kSR) {
+    const unsigned p = off + q;
+    int NP[3];
+    const unsigned cnt = s_cnt[q];
+    const unsigned char st = sir_advance(p, r, B.a, cnt, step, NP);
+    B.ninf[p] = cnt;
+    c0 += st == 0 ? 1u : 0u;
+    c1 += st == 1 ? 1u : 0u;
+    c2 += st == 2 ? 1u : 0u;
+  }
+  auto add = [](unsigned a, unsigned b) { return a + b; };
+  c0 = warp_reduce(c0, add);
+  c1 = warp_reduce(c1, add);
+  c2 = warp_reduce(c2, add);
+  if ((t & 31u) == 0) {
+    if (c0) atomicAdd(&s_c[0], c0);
+    if (c1) atomicAdd(&s_c[1], c1);
+    if (c2) atomicAdd(&s_c[2], c2);
+  }
+  __syncthreads();
+  if (t < 3) B.hist[(size_t)(step % B.hist_len) * B.runs * 3u + 3u * ri + t] = s_c[t];
+}
+
 // Evaluate the device Philox generator on n (counter, key) pairs.
 __global__ void k_philox(unsigned n, const uint4* __restrict__ ctr, const uint2* __restrict__ key,
                          uint4* __restrict__ out) {
@@ -388,6 +532,27 @@ cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_sir_ensemble, B, g, (unsigned)blocks + barrier_extra,
                             spin_limit);
+}
+
+// Dynamic shared memory of the per-run kernel for runs of up to `words` (nb^3 + 1 + agents) words;
+// 0 when it does not fit on this device.
+size_t sir_runs_smem_bytes(size_t words) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  const size_t bytes = words * sizeof(unsigned);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k_sir_runs) != cudaSuccess) return 0;
+  if (bytes + fa.sharedSizeBytes > (size_t)optin) return 0;
+  if (cudaFuncSetAttribute(k_sir_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return 0;
+  return bytes;
+}
+
+void launch_sir_runs(cudaStream_t s, const SirBatchDev& B, DevGrid* g, size_t smem_bytes) {
+  k_sir_runs<<<B.runs, kSR, smem_bytes, s>>>(B, g);
+  launch_step_done(s, g);
 }
 
 int sir_ensemble_blocks_per_sm() {

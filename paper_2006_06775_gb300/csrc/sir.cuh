@@ -78,6 +78,10 @@ void launch_sir_step(cudaStream_t s, const SirSingle& S, DevGrid* g, int grid_bl
 cudaError_t launch_sir_ensemble(cudaStream_t s, const SirBatchDev& B, DevGrid* g, int blocks,
                                 unsigned barrier_extra, unsigned spin_limit, bool cooperative);
 int sir_ensemble_blocks_per_sm();
+// One CTA per run (histogram, scan and counts in shared memory); sir_runs_smem_bytes returns the
+// dynamic shared memory for runs of up to `words` = nb^3 + 1 + agents words, or 0 if it does not fit.
+size_t sir_runs_smem_bytes(size_t words);
+void launch_sir_runs(cudaStream_t s, const SirBatchDev& B, DevGrid* g, size_t smem_bytes);
 void launch_philox(cudaStream_t s, unsigned n, const uint4* ctr, const uint2* key, uint4* out);
 
 }  // namespace bdm

@@ -30,10 +30,11 @@ def uneven_runs():
     return out
 
 
-def test_batch_matches_single_handles_and_history():
+@pytest.mark.parametrize("persistent_only", [False, True])
+def test_batch_matches_single_handles_and_history(persistent_only):
     runs = uneven_runs()
     steps = 25
-    batch = bdm.Batch([p for p, _ in runs], history_steps=64)
+    batch = bdm.Batch([p for p, _ in runs], history_steps=64, persistent_only=persistent_only)
     for k, (_, inp) in enumerate(runs):
         batch.add_agents(k, inp["x"], inp["y"], inp["z"], inp["sir_state"])
     batch.step(10)
@@ -56,10 +57,11 @@ def test_batch_matches_single_handles_and_history():
         single.close()
 
 
-def test_batch_matches_oracle():
+@pytest.mark.parametrize("persistent_only", [False, True])
+def test_batch_matches_oracle(persistent_only):
     all_runs = uneven_runs()
     runs = [all_runs[k] for k in (0, 1, 2, 6)]  # sparse, single agent, 3 boxes, dense infection
-    batch = bdm.Batch([p for p, _ in runs])
+    batch = bdm.Batch([p for p, _ in runs], persistent_only=persistent_only)
     refs = []
     for k, (p, inp) in enumerate(runs):
         batch.add_agents(k, inp["x"], inp["y"], inp["z"], inp["sir_state"])
@@ -95,10 +97,12 @@ def test_barrier_wait_that_runs_out_is_reported():
     assert np.array_equal(ok.get_state(0)["sir_state"], ref.get_state()["sir_state"])
 
 
-def test_full_ensemble_sampled_runs():
+@pytest.mark.parametrize("boxes", [32, 40])
+def test_full_ensemble_sampled_runs(boxes):
     """256 runs x 20,000 persons, the ensemble workload: sampled runs equal their single-run
-    handles after 200 steps, and every step's counts sum to the run size."""
-    ens = synth.sir_ensemble()
+    handles after 200 steps, and every step's counts sum to the run size (32 boxes per axis: one CTA
+    per run in shared memory; 40: the persistent grid)."""
+    ens = [(dict(p, sir_boxes=boxes), inp) for p, inp in synth.sir_ensemble()]
     batch = bdm.Batch([p for p, _ in ens], history_steps=200)
     for k, (_, inp) in enumerate(ens):
         batch.add_agents(k, inp["x"], inp["y"], inp["z"], inp["sir_state"])
