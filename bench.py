@@ -569,10 +569,14 @@ def bench_serving(count):
             enumerate(("mechanics", "sir"))]
     wp = {r.rid: serve.payload(r) for r in warm}
     serve.run_one_at_a_time(serve.GpuExecutor(1), warm, lambda r: wp[r.rid])
-    served = serve.Server(serve.GpuExecutor(streams=8), budget_bytes=150e9, max_active=64,
-                          chunk=25).run(reqs, lambda r: payloads[r.rid])
+    # served: neighbour lists (the tuned 2.5 um skin) for mechanics, 16 streams; the baseline runs
+    # the same trace one simulation at a time with the plain kernels (grid rebuilt every step)
+    served = serve.Server(serve.GpuExecutor(streams=16, mechanics_skin=2.5), budget_bytes=150e9,
+                          max_active=64, chunk=25).run(reqs, lambda r: payloads[r.rid])
     alone = serve.run_one_at_a_time(serve.GpuExecutor(streams=1), reqs, lambda r: payloads[r.rid])
     out = serve.summarize(served)
+    out["mechanics_skin_um"] = 2.5
+    out["streams"] = 16
     out["one_at_a_time"] = serve.summarize(alone)
     out["trace"] = "first %d requests of the Poisson stream (seed 4)" % count
     return out

@@ -20,7 +20,9 @@ import numpy as np
 
 from . import synth
 
-MECH_BYTES_PER_AGENT = 124 + 8 * 3   # agent arrays + ~3 boxes per agent (count/start, capacity)
+# agent arrays + ~3 boxes per agent (count/start, capacity) + the neighbour-list mode's lists (32
+# entries), second position set, list length and move
+MECH_BYTES_PER_AGENT = 124 + 8 * 3 + 128 + 40 + 8
 SIR_BYTES_PER_AGENT = 13 + 5 * 4 + 8 + 8   # state, 5 words per agent, list entry, ~1 box each
 MIN_BYTES = 4 << 20
 
@@ -152,18 +154,23 @@ def payload(req):
 
 
 class GpuExecutor:
-    """Each simulation gets a libbdm handle on one of `streams` CUDA streams (round robin)."""
+    """Each simulation gets a libbdm handle on one of `streams` CUDA streams (round robin).
+    `mechanics_skin` > 0 runs mechanics requests with neighbour lists of that skin (um; the
+    interaction radius is then the request's largest diameter)."""
 
-    def __init__(self, streams=8):
+    def __init__(self, streams=8, mechanics_skin=0.0):
         import torch
         from . import bdm
         self.torch = torch
         self.bdm = bdm
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.next = 0
+        self.skin = float(mechanics_skin)
 
     def start(self, req, pl):
         params, inp = pl
+        if params["kind"] != "sir" and self.skin > 0.0:
+            params = dict(params, interaction_radius=float(np.max(inp["diameter"])), skin=self.skin)
         s = self.streams[self.next % len(self.streams)]
         self.next += 1
         sim = self.bdm.Sim(params, stream=s)

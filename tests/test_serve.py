@@ -105,18 +105,20 @@ def test_summary_statistics():
 
 
 @pytest.mark.gpu
-def test_served_results_equal_results_alone():
+@pytest.mark.parametrize("skin", [0.0, 2.5])
+def test_served_results_equal_results_alone(skin):
     """A small mixed trace served concurrently gives, for every request, exactly the result of
-    the same simulation run alone."""
+    the same simulation run alone (with the grid rebuilt every step, and with neighbour lists)."""
     g = synth.rng(4, 77)
     reqs = [synth.Request(k, 0.002 * k, "mechanics" if k % 3 else "sir",
                           int(g.integers(1000, 20000)), int(g.integers(20, 60)), 900 + k)
             for k in range(12)]
     payloads = {r.rid: serve.payload(r) for r in reqs}
-    ex = serve.GpuExecutor(streams=4)
+    ex = serve.GpuExecutor(streams=4, mechanics_skin=skin)
     mixed = serve.Server(ex, budget_bytes=150e9, max_active=8, chunk=7).run(
         reqs, lambda r: payloads[r.rid])
-    alone = serve.run_one_at_a_time(serve.GpuExecutor(streams=1), reqs, lambda r: payloads[r.rid])
+    alone = serve.run_one_at_a_time(serve.GpuExecutor(streams=1, mechanics_skin=skin), reqs,
+                                    lambda r: payloads[r.rid])
     A = {j.req.rid: j.result for j in alone}
     assert len(mixed) == len(reqs)
     for j in mixed:
