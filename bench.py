@@ -282,9 +282,12 @@ def run_ours(args):
     per_launch = {k: v[1] / max(v[0], 1) for k, v in ktimes.items()}
     share = {k: v[1] for k, v in ktimes.items()}
     dom = max(share, key=lambda k: share[k])
-    # the force kernels are issue/ALU-bound (ncu: DRAM well below peak, issue ~55-69 % active): the
-    # roofline is FP32 arithmetic; the HBM view of the same launch is reported beside it.  With a
-    # skin the dominant kernel evaluates neighbour lists (9 FLOP per listed pair + 13 per agent).
+    # Roofline of the dominant kernel: its algorithmic intensity (~0.6 FLOP per algorithmic byte with
+    # a skin, ~1.3 without) is far below the machine balance of ~12 FLOP/B (FP32 peak over the
+    # measured copy bandwidth), so its roofline is HBM bandwidth.  The kernel does not reach it
+    # because it is issue-bound (ncu: ~63 % issue active, DRAM ~37 %); the FP32 view of the same
+    # launch is reported beside it.  With a skin the dominant kernel evaluates neighbour lists
+    # (9 FLOP per listed pair + 13 per agent).
     st1 = sim.get_state(fields=())
     skin = float(params.get("skin", 0.0))
     rebuilds_timed = int(st1["grid_rebuilds"]) - int(st0["grid_rebuilds"])
@@ -305,15 +308,14 @@ def run_ours(args):
     mech_ms = sum(v[1] for k, v in ktimes.items() if k != "ftcs") / args.steps
     step_bytes = STEP_BYTES_PER_AGENT(boxes_per_agent) * n + 8.0 * 512 ** 3
     step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": fkernel, "achieved": achieved_tf,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                "traffic": measured_traffic(fkernel, n),
-                "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz)",
-                "alg_flop_per_agent": flop_pa,
+    roofline = {"bound": "hbm", "kernel": fkernel, "achieved": achieved_gb, "peak": peak,
+                "unit": "GB/s", "frac": achieved_gb / peak, "traffic": measured_traffic(fkernel, n),
+                "peak_kind": peak_kind, "alg_bytes_per_agent": bytes_pa,
+                "alg_flop_per_byte": flop_pa / bytes_pa,
                 "dominant_kernel_by_time": dom,
-                "hbm": {"achieved": achieved_gb, "peak": peak, "unit": "GB/s",
-                        "frac": achieved_gb / peak, "peak_kind": peak_kind,
-                        "alg_bytes_per_agent": bytes_pa}}
+                "fp32": {"achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / FP32_PEAK_TFLOPS, "alg_flop_per_agent": flop_pa,
+                         "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz)"}}
 
     diffusion = None
     if "ftcs" in per_launch:
