@@ -557,7 +557,10 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
         if (still) atomicAdd(&s_skip, 1u);
       }
       const unsigned m = still ? 0u : s_m[buf][t];
-      for (unsigned k0 = 0; k0 < m; k0 += 4) {
+      // the warp runs to its longest list (a uniform bound: no lane leaves the loop early; slots
+      // past a lane's list are evaluated as far away and add nothing)
+      const unsigned mw = __reduce_max_sync(__activemask(), m);  // lanes past n have left the loop
+      for (unsigned k0 = 0; k0 < mw; k0 += 4) {
         unsigned v[4];
         if (k0 == 0) {
 #pragma unroll
@@ -570,28 +573,32 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
         float4 q[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (k0 + (unsigned)u < m) q[u] = __ldg(p4 + (v[u] >> 5));
-        // most listed candidates are neighbours: decided here, in list order, without staging
+          q[u] = k0 + (unsigned)u < m ? __ldg(p4 + (v[u] >> 5)) : make_float4(3.0e4f, 3.0e4f, 3.0e4f, 0.f);
+        // the four entries are evaluated without branches (a slot past the list is far away, so it
+        // neither counts nor touches); their contributions are added in list order
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (k0 + (unsigned)u >= m) break;
-          const unsigned j = v[u] >> 5, cc = v[u] & 31u;
-          const float4 sh = s_shift[cc];
+          const unsigned cc = v[u] & 31u;
+          const float4 sh = s_shift[k0 + (unsigned)u < m ? cc : 13u];
           const float ex = (pi.x + sh.x) - q[u].x;
           const float ey = (pi.y + sh.y) - q[u].y;
           const float ez = (pi.z + sh.z) - q[u].z;
           const float dd = ex * ex + ey * ey + ez * ez;
-          if (dd <= R2hi) {
-            if (dd < R2lo) {
-              ++cnt;
-            } else {  // near R: queued for the FP64 decision after the loop
-              if (nband < (unsigned)kBQ) s_bq[nband][t] = j;
-              ++nband;
-            }
-            const float rs = pi.w + q[u].w;
-            if (dd < rs * rs && dd > 0.f)
-              contact_force(Fx, Fy, Fz, ex, ey, ez, pi.w, q[u].w, c.kf, c.gammaf);
+          cnt += dd < R2lo ? 1u : 0u;
+          if (dd >= R2lo && dd <= R2hi) {  // near R: queued for the FP64 decision after the loop
+            if (nband < (unsigned)kBQ) s_bq[nband][t] = v[u] >> 5;
+            ++nband;
           }
+          const float rs = pi.w + q[u].w;
+          const float rinv = rsqrtf(dd);
+          const float delta = rs - dd * rinv;
+          const float rd = __fdividef(pi.w * q[u].w, rs) * delta;
+          const float F = c.kf * delta - c.gammaf * (rd * rsqrtf(rd));
+          const float sc = F * rinv;
+          const bool touch = dd <= R2hi && dd < rs * rs && dd > 0.f && delta > 0.f;
+          Fx = touch ? fmaf(sc, ex, Fx) : Fx;
+          Fy = touch ? fmaf(sc, ey, Fy) : Fy;
+          Fz = touch ? fmaf(sc, ez, Fz) : Fz;
         }
       }
       if (nband > (unsigned)kBQ) {
