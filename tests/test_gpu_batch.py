@@ -119,3 +119,27 @@ def test_full_ensemble_sampled_runs(boxes):
         for f in FIELDS:
             assert np.array_equal(got[f], want[f]), (k, f)
         single.close()
+
+
+@pytest.mark.parametrize("persistent_only", [False, True])
+def test_batch_with_an_empty_run(persistent_only):
+    """A run without agents sits between two others: it reports zero counts, and its neighbours
+    still match the oracle."""
+    all_runs = uneven_runs()
+    runs = [all_runs[0], (dict(all_runs[2][0], run_id=50), None), all_runs[2]]
+    batch = bdm.Batch([p for p, _ in runs], history_steps=8, persistent_only=persistent_only)
+    for k, (_, inp) in enumerate(runs):
+        if inp is not None:
+            batch.add_agents(k, inp["x"], inp["y"], inp["z"], inp["sir_state"])
+    batch.step(6)
+    empty = batch.get_state(1)
+    assert empty["n"] == 0 and np.array_equal(empty["sir_counts"], [0, 0, 0])
+    for k in (0, 2):
+        p, inp = runs[k]
+        ref = oracle.OracleSim(p)
+        ref.add_agents(inp["x"], inp["y"], inp["z"], sir_state=inp["sir_state"])
+        ref.step(6)
+        want, got = ref.get_state(), batch.get_state(k)
+        for f in ("x", "y", "z", "sir_state", "neighbour_count", "box_id", "sir_counts"):
+            assert np.array_equal(got[f], want[f]), (k, f)
+    batch.close()
