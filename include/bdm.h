@@ -64,7 +64,10 @@ typedef struct bdm_params {
   double repulsion;              /* k in F = k delta - gamma sqrt(rho delta)                       */
   double attraction;             /* gamma                                                          */
   double max_displacement;       /* cap on |displacement| per step                                 */
-  double interaction_radius;     /* neighbour radius R; 0 = largest diameter, every step          */
+  double interaction_radius;     /* neighbour radius R; 0 = largest diameter, every step.  With
+                                    BDM_MIXED, R must be at least the largest diameter (contacts
+                                    are found among the pairs within R); a step that finds a
+                                    larger diameter fails with BDM_ESTATE                        */
   double box_length;             /* grid box L >= R + skin; 0 = R + skin                           */
   double skin;                   /* neighbour-list skin (mixed precision without growth; 0 = off):
                                     the grid is rebuilt and each agent's candidates within R + skin

@@ -401,6 +401,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     mc.skin_half = (float)(0.5 * p.skin * (1.0 - 1e-5));
     mc.max_cadence = 64;
     mc.skip_stationary = p.skip_stationary ? 1 : 0;
+    mc.mixed = s->mixed ? 1 : 0;
   }
   if (s->diffusion) {
     const size_t nv = (size_t)p.grid_n[0] * p.grid_n[1] * p.grid_n[2];
@@ -440,7 +441,8 @@ int decode_err(bdm_sim* s, unsigned e) {
   if (e & ERR_CAPACITY)
     return fail(s, BDM_ENOMEM, "division would exceed the agent capacity (%zu)", s->capacity);
   if (e & ERR_RADIUS)
-    return fail(s, BDM_ESTATE, "invalid grid: radius/box length or agent extent out of range");
+    return fail(s, BDM_ESTATE, "invalid grid: radius/box length or agent extent out of range (mixed "
+                               "precision needs interaction_radius >= the largest diameter)");
   return fail(s, BDM_ESTATE, "device index check failed (error bits 0x%x)", e);
 }
 

@@ -83,6 +83,7 @@ struct MechConsts {               // per-simulation constants passed by value
   float skin_half;                // rebuild when an agent may have moved more than this
   unsigned max_cadence;           // rebuild at least every this many steps (bounds FP32 drift)
   int skip_stationary;            // list steps skip agents that, with their listed neighbours, stood still
+  int mixed;                      // mixed precision: contacts are searched within R only
 };
 
 // ---- exact helpers -------------------------------------------------------------------------

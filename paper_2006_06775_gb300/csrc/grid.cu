@@ -44,6 +44,8 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
                                           : (double)__uint_as_float(g->acc_maxdiam);
     double L = c.box_length > 0.0 ? c.box_length : R + c.skin;
     bool ok = (R > 0.0) && (L >= R + c.skin) && (L < 2048.0);
+    // the mixed path finds contacts among the pairs within R, so R may not be below a diameter
+    if (c.mixed && R < (double)__uint_as_float(g->acc_maxdiam)) ok = false;
     long long Lq = (long long)ceil(L * kQScale);
     unsigned long long nbox = 1;
     long long O[3];

@@ -389,3 +389,20 @@ def test_invalid_agents_are_rejected_and_handle_stays_usable():
     sim.step(2)
     ref.step(2)
     assert_step_equal(sim.get_state(), ref.get_state())
+
+
+def test_mixed_radius_below_a_diameter_is_refused():
+    """Mixed precision finds contacts among the pairs within R: an interaction radius below the
+    largest diameter is reported (BDM_ESTATE) instead of silently dropping contacts."""
+    params, inp = synth.plain_mechanics()
+    sim = bdm.Sim(dict(params, precision="mixed", interaction_radius=9.0))
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    sim.step(1)
+    with pytest.raises(bdm.BdmError) as e:
+        sim.get_state()
+    assert e.value.code == bdm.BDM_ESTATE
+    sim.close()
+    ok = bdm.Sim(dict(params, precision="mixed", interaction_radius=12.0))
+    ok.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    ok.step(1)
+    assert ok.get_state(fields=())["n"] == len(inp["x"])
