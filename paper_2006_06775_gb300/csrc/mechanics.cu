@@ -592,8 +592,10 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
           const float rs = pi.w + q[u].w;
           const float rinv = rsqrtf(dd);
           const float delta = rs - dd * rinv;
-          const float rd = __fdividef(pi.w * q[u].w, rs) * delta;
-          const float F = c.kf * delta - c.gammaf * (rd * rsqrtf(rd));
+          // sqrt(rho delta) = sqrt(ri rj delta / rs) = p rsqrt(p rs) with p = ri rj delta: one
+          // reciprocal square root instead of a reciprocal and a reciprocal square root
+          const float pp = (pi.w * q[u].w) * delta;
+          const float F = c.kf * delta - c.gammaf * (pp * rsqrtf(pp * rs));
           const float sc = F * rinv;
           const bool touch = dd <= R2hi && dd < rs * rs && dd > 0.f && delta > 0.f;
           Fx = touch ? fmaf(sc, ex, Fx) : Fx;
