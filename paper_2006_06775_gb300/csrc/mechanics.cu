@@ -699,9 +699,11 @@ __global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p
     const unsigned q0 = b / (unsigned)d0;
     const int iy = (int)(q0 % (unsigned)d1), iz = (int)(q0 / (unsigned)d1);
     const float4 pi = __ldg(p4 + i);
-    unsigned nr = 0;
+    unsigned nr = 0, pb1 = 0, pb2 = 0;  // runs in all, before the dz = 0 plane, before dz = +1
 #pragma unroll
     for (int sg = 0; sg < 9; ++sg) {
+      if (sg == 3) pb1 = nr;
+      if (sg == 6) pb2 = nr;
       const int jz = iz + sg / 3 - 1, jy = iy + sg % 3 - 1;
       if (jz < 0 || jz >= d2 || jy < 0 || jy >= d1) continue;
       const unsigned row = ((unsigned)jz * (unsigned)d1 + (unsigned)jy) * (unsigned)d0 + (unsigned)ix;
@@ -711,9 +713,13 @@ __global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p
       if (e3 > e0) s_run[nr++][t] = make_uint4(e0 | ((unsigned)sg << 27), e1, e2, e3);
     }
     unsigned ln = 0;
-    if (nr) {
-      unsigned r = 0;
-      uint4 run = s_run[0][t];
+    // one loop per z plane of three rows: the warp's lanes stay within the same three row ranges
+    // (shared cache lines), and wait only for the lane with the most candidates in the plane
+    for (int pl = 0; pl < 3; ++pl) {
+      unsigned r = pl == 0 ? 0u : (pl == 1 ? pb1 : pb2);
+      const unsigned r1 = pl == 0 ? pb1 : (pl == 1 ? pb2 : nr);
+      if (r == r1) continue;
+      uint4 run = s_run[r][t];
       unsigned j = run.x & 0x7FFFFFFu, cb = (run.x >> 27) * 3u;
       float py = pi.y - (float)((int)(run.x >> 27) % 3 - 1) * Lf;
       float pz = pi.z - (float)((int)(run.x >> 27) / 3 - 1) * Lf;
@@ -728,8 +734,8 @@ __global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p
           if (ln < (unsigned)kListCap) list[list_at(i, ln)] = (j << 5) | (cb + bx);
           ++ln;
         }
-        if (++j == run.w) {  // next row run
-          if (++r == nr) break;
+        if (++j == run.w) {  // next row run of the plane
+          if (++r == r1) break;
           run = s_run[r][t];
           j = run.x & 0x7FFFFFFu;
           cb = (run.x >> 27) * 3u;
