@@ -4,10 +4,13 @@ A plain, slow, obviously correct restatement of what one simulation step compute
 tests, by ``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``.  The product
 library never imports or links it and shares no code with it.  Each function cites the passage of
 BioDynaMo (arXiv 2006.06775) it follows, or the reading of the paper that fills a gap (readings
-R1-R11 are listed with their justification in the design notes at the repository root).
+R1-R14 are listed with their justification in the design notes at the repository root).
 
 Functions without an independent pin: the daughter offset distance and the division axis law (R7)
 are readings the paper does not fix; their tests check internal consistency only (parity unpinned).
+The oncology behaviours (Brownian migration R13, apoptosis R14) are readings too: the paper names
+them but prints neither law nor rate.  Their tests pin distributional facts (standard normal
+deviates, binomial survival, order kept), not the paper's parameters.
 """
 import ctypes
 import math
@@ -49,6 +52,12 @@ def lib():
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.POINTER(ctypes.c_size_t)]
+        L.orc_apoptosis.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, _f32p, _f64p,
+                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.c_uint32]
+        L.orc_apoptosis.restype = ctypes.c_size_t
+        L.orc_brownian.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, ctypes.c_double,
+                                   ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
         L.orc_secrete.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, _f64p, _i64p, _f64p,
                                   ctypes.c_double, ctypes.c_double]
         L.orc_ftcs.argtypes = [_i64p, _f64p, _f64p, ctypes.c_double, ctypes.c_double]
@@ -147,6 +156,24 @@ def grow_divide(x, y, z, diam, vol, growth_volume, division_volume, offset_frac,
                           run & 0xFFFFFFFF, step & 0xFFFFFFFF, ctypes.byref(n_out))
     m = n_out.value
     return {k: v[:m].copy() for k, v in arrs.items()}
+
+
+def apoptosis(x, y, z, diam, vol, p_apoptosis, seed, run, step):
+    """Apoptosis at step start (reading R14).  Returns the survivors' arrays (order kept)."""
+    arrs = {"x": _f64(x).copy(), "y": _f64(y).copy(), "z": _f64(z).copy(),
+            "diameter": _f32(diam).copy(), "volume": _f64(vol).copy()}
+    m = lib().orc_apoptosis(len(x), arrs["x"], arrs["y"], arrs["z"], arrs["diameter"],
+                            arrs["volume"], probability_threshold(p_apoptosis), seed & 0xFFFFFFFF,
+                            run & 0xFFFFFFFF, step & 0xFFFFFFFF)
+    return {k: v[:m].copy() for k, v in arrs.items()}
+
+
+def brownian(x, y, z, sigma, seed, run, step):
+    """Brownian migration after the mechanical update (reading R13); returns new x, y, z."""
+    x, y, z = _f64(x).copy(), _f64(y).copy(), _f64(z).copy()
+    lib().orc_brownian(len(x), x, y, z, float(sigma), seed & 0xFFFFFFFF, run & 0xFFFFFFFF,
+                       step & 0xFFFFFFFF)
+    return x, y, z
 
 
 def secrete(x, y, z, grid_values, origin, voxel, amount):
@@ -271,6 +298,12 @@ class OracleSim:
     # -- execution ------------------------------------------------------------------------------
     def _mech_one(self):
         p = self.p
+        if p.get("p_apoptosis", 0.0) > 0.0 and self.n:
+            r = apoptosis(self.x, self.y, self.z, self.diameter, self.volume, p["p_apoptosis"],
+                          p.get("seed", 0), p.get("run_id", 0), self.step_index)
+            self.x, self.y, self.z = r["x"], r["y"], r["z"]
+            self.diameter, self.volume = r["diameter"], r["volume"]
+            self.n = len(self.x)
         if p.get("growth_enabled"):
             r = grow_divide(self.x, self.y, self.z, self.diameter, self.volume, p["growth_volume"],
                             p["division_volume"], p["division_offset_frac"], p.get("seed", 0),
@@ -285,6 +318,10 @@ class OracleSim:
             self.x, self.y, self.z = r["x"], r["y"], r["z"]
             self.neighbour_count, self.box_id, self.last_grid = (r["neighbour_count"], r["box_id"],
                                                                  r["grid"])
+            if p.get("brownian_sigma", 0.0) > 0.0:
+                self.x, self.y, self.z = brownian(self.x, self.y, self.z, p["brownian_sigma"],
+                                                  p.get("seed", 0), p.get("run_id", 0),
+                                                  self.step_index)
         if p.get("diffusion_enabled"):
             if p.get("secretion", 0.0):
                 secrete(self.x, self.y, self.z, self.grid, p["grid_origin"], p["voxel"],

@@ -307,6 +307,53 @@ int orc_grow_divide(size_t n, double* x, double* y, double* z, float* diam, doub
 }
 
 /* ------------------------------------------------------------------------------------------------
+ * Apoptosis (paper Sec. "Oncology use case": cell apoptosis is one of the modelled mechanisms; its
+ * rate is not printed).  Reading R14: at the start of a step every agent dies with probability p:
+ * Philox4x32-10 with key (seed, run) and counter (id, step, 4, 0) gives w, and the agent dies when
+ * w_0 < floor(p 2^32).  Survivors keep their relative order and take the dense ids 0..m-1.
+ * ------------------------------------------------------------------------------------------------ */
+size_t orc_apoptosis(size_t n, double* x, double* y, double* z, float* diam, double* vol,
+                     uint64_t thr, uint32_t seed_lo, uint32_t run, uint32_t step) {
+  const uint32_t key[2] = {seed_lo, run};
+  size_t m = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t ctr[4] = {(uint32_t)i, step, 4u, 0u};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    if ((uint64_t)w[0] < thr) continue;
+    x[m] = x[i]; y[m] = y[i]; z[m] = z[i];
+    diam[m] = diam[i];
+    vol[m] = vol[i];
+    ++m;
+  }
+  return m;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Brownian migration (paper Sec. "Oncology use case": migration is modelled as Brownian motion;
+ * its amplitude is not printed).  Reading R13: after the capped mechanical update every agent moves
+ * by sigma (g0, g1, g2), standard normal deviates by the Box-Muller transform of Philox4x32-10 words
+ * (key (seed, run), counter (id, step, 3, 0)): with u = (w0 + 1) 2^-32, v = w1 2^-32,
+ * u' = (w2 + 1) 2^-32, v' = w3 2^-32: g0 = sqrt(-2 ln u) cos(2 pi v), g1 = sqrt(-2 ln u) sin(2 pi v),
+ * g2 = sqrt(-2 ln u') cos(2 pi v').  Each coordinate: x <- x + sigma g (after x <- x + D).
+ * ------------------------------------------------------------------------------------------------ */
+void orc_brownian(size_t n, double* x, double* y, double* z, double sigma, uint32_t seed_lo,
+                  uint32_t run, uint32_t step) {
+  const uint32_t key[2] = {seed_lo, run};
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t ctr[4] = {(uint32_t)i, step, 3u, 0u};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    const double u = ldexp((double)w[0] + 1.0, -32), v = ldexp((double)w[1], -32);
+    const double u2 = ldexp((double)w[2] + 1.0, -32), v2 = ldexp((double)w[3], -32);
+    const double r = sqrt(-2.0 * log(u)), r2 = sqrt(-2.0 * log(u2));
+    x[i] = x[i] + sigma * (r * cos(2.0 * ORC_PI * v));
+    y[i] = y[i] + sigma * (r * sin(2.0 * ORC_PI * v));
+    z[i] = z[i] + sigma * (r2 * cos(2.0 * ORC_PI * v2));
+  }
+}
+
+/* ------------------------------------------------------------------------------------------------
  * Secretion into a substance grid (paper Sec. "Simulation concepts": growth-factor secretion is an
  * agent behaviour acting on the extracellular substance).  Reading R8: voxel index per axis is
  * clamp(floor((x - origin) / h), 0, dims - 1); every agent adds q.

@@ -61,6 +61,12 @@ int orc_mech_step(size_t n, const double* x, const double* y, const double* z, c
 int orc_grow_divide(size_t n, double* x, double* y, double* z, float* diam, double* vol,
                     double dv, double vdiv, double offset_frac, uint32_t seed_lo, uint32_t run,
                     uint32_t step, size_t* n_out);
+/* Apoptosis at step start (reading R14): removes the agents that die, keeps the order; returns m. */
+size_t orc_apoptosis(size_t n, double* x, double* y, double* z, float* diam, double* vol,
+                     uint64_t thr, uint32_t seed_lo, uint32_t run, uint32_t step);
+/* Brownian migration after the mechanical update (reading R13). */
+void orc_brownian(size_t n, double* x, double* y, double* z, double sigma, uint32_t seed_lo,
+                  uint32_t run, uint32_t step);
 
 /* Secretion (reading R8): each agent adds q to the voxel that holds its centre (clamped). */
 void orc_secrete(size_t n, const double* x, const double* y, const double* z, double* grid,
