@@ -331,10 +331,11 @@ def run_ours(args):
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
 
     sim.close()
-    ensemble = serving = plain = spheroid = stationary = None
+    ensemble = serving = plain = spheroid = stationary = oncology = None
     if rank == 0 and not args.no_small:
         plain = bench_plain()
         spheroid = bench_spheroid()
+        oncology = bench_oncology()
         stationary = bench_stationary()
     if rank == 0 and not args.no_ensemble:
         ensemble = bench_ensemble(args.ensemble_steps, args.ensemble_baseline_runs)
@@ -372,7 +373,8 @@ def run_ours(args):
             "kernels_ms_per_launch": {k: round(v, 4) for k, v in per_launch.items()},
             "diffusion": diffusion,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
-            "plain": plain, "spheroid": spheroid, "stationary": stationary, "ensemble": ensemble,
+            "plain": plain, "spheroid": spheroid, "oncology": oncology, "stationary": stationary,
+            "ensemble": ensemble,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -478,6 +480,26 @@ def fp64_peak_tflops(n=4096, reps=5):
     stream = torch.cuda.current_stream()
     ms = _event_time_ms(stream, lambda: [torch.matmul(a, b) for _ in range(reps)])
     return 2.0 * n ** 3 * reps / (ms * 1e-3) / 1e12
+
+
+def bench_oncology(steps=100, p_apoptosis=0.02, sigma=0.5):
+    """The tumour spheroid with the oncology behaviours (apoptosis at step start, Brownian migration
+    after the update) and secretion into the co-stepped 128^3 grid: `steps` steps after one
+    warm-up step, timed on the device."""
+    from paper_2006_06775_gb300 import bdm
+    params, inp = synth.spheroid()
+    params = dict(params, capacity=1 << 21, p_apoptosis=p_apoptosis, brownian_sigma=sigma)
+    sim = bdm.Sim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    sim.step(1)
+    n0 = int(sim.get_state(fields=())["n"])
+    ms = _event_time_ms(sim.stream, lambda: sim.step(steps))
+    n1 = int(sim.get_state(fields=())["n"])
+    sim.close()
+    return {"workload": "tumour spheroid (512 cells) with apoptosis p = %g per step and Brownian "
+                        "migration sigma = %g um, growth, division and secretion into a 128^3 grid"
+                        % (p_apoptosis, sigma),
+            "steps": steps, "agents_start": n0, "agents_end": n1, "ms_per_step": ms / steps}
 
 
 def bench_stationary(n=10_000_000, steps=10, warmup=3, skin=2.5):

@@ -113,6 +113,11 @@ typedef struct bdm_params {
      count again, so it can be left out.  The results are identical either way. */
   int32_t skip_stationary;       /* 1 = skip such agents; 0 = evaluate every agent every step     */
   int32_t reserved4;
+  /* Oncology behaviours (readings R13, R14; the grid is then rebuilt every step, skin = 0). */
+  double brownian_sigma;         /* Brownian migration: after the capped mechanical update every
+                                    agent moves by sigma * N(0,1) per axis (um); 0 = off          */
+  double p_apoptosis;            /* each agent dies at the start of a step with this probability;
+                                    survivors keep their order and take dense ids; 0 = off       */
   /* Device plumbing. */
   void* stream;                  /* cudaStream_t, NULL = a stream the handle creates              */
   void* (*alloc)(size_t bytes, void* user); /* optional device allocator                         */

@@ -222,8 +222,14 @@ int check_params(bdm_sim* s, const bdm_params* p) {
     if (p->box_length > 0.0 && p->interaction_radius > 0.0 &&
         p->box_length < p->interaction_radius + p->skin)
       return fail(s, BDM_EINVAL, "box_length below interaction_radius + skin");
-    if (p->skin > 0.0 && (p->precision != BDM_MIXED || p->growth_enabled || p->force_variant != 0))
-      return fail(s, BDM_EINVAL, "a neighbour-list skin needs mixed precision, no growth, force_variant 0");
+    if (!(p->brownian_sigma >= 0.0) || !std::isfinite(p->brownian_sigma))
+      return fail(s, BDM_EINVAL, "brownian_sigma must be finite and >= 0");
+    if (!(p->p_apoptosis >= 0.0 && p->p_apoptosis <= 1.0))
+      return fail(s, BDM_EINVAL, "p_apoptosis must be in [0, 1]");
+    if (p->skin > 0.0 && (p->precision != BDM_MIXED || p->growth_enabled || p->force_variant != 0 ||
+                          p->brownian_sigma > 0.0 || p->p_apoptosis > 0.0))
+      return fail(s, BDM_EINVAL, "a neighbour-list skin needs mixed precision, force_variant 0 and no "
+                                 "growth, apoptosis or Brownian migration");
     if (p->growth_enabled) {
       if (!(p->growth_volume >= 0.0) || !(p->division_volume > 0.0) ||
           !(p->division_offset_frac >= 0.0))
@@ -375,7 +381,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
     }
     b.max_tiles = scan_tiles_for(boxcap + 1);
     if ((rc = dalloc_n(s, &b.tiles[0], b.max_tiles))) return rc;
-    if (s->growth) {
+    if (s->growth || p.p_apoptosis > 0.0) {
       if ((rc = dalloc_n(s, &b.tiles[1], scan_tiles_for(C + 1))) ||
           (rc = dalloc_n(s, &b.flag, C + 1)) || (rc = dalloc_n(s, &b.drank, C + 1)))
         return rc;
@@ -487,15 +493,27 @@ int enqueue_mech_step(bdm_sim* s) {
   cudaStream_t st = s->stream;
   const bdm_params& p = s->p;
   MechBuffers& b = s->mb;
-  const AgentArrays A = b.attr[s->attr_cur], B = b.attr[s->attr_cur ^ 1];
+  AgentArrays A = b.attr[s->attr_cur], B = b.attr[s->attr_cur ^ 1];
   DevGrid* g = s->g;
+  const uint2 pkey = make_uint2((unsigned)(p.seed & 0xFFFFFFFFull), p.run_id);
+  if (p.p_apoptosis > 0.0) {  // R14: deaths at step start; survivors to the other attribute buffer
+    const unsigned long long thr = (unsigned long long)std::floor(p.p_apoptosis * 4294967296.0);
+    RUN("apo_flag", 1, launch_apoptosis_flags(st, b, A, g, thr, pkey, s->blocks_stream));
+    CK(cudaMemsetAsync(b.tiles[1], 0, sizeof(unsigned long long) * scan_tiles_for(s->capacity + 1), st));
+    RUN("scan_apo", 1, launch_scan(st, b.flag, b.drank, &g->ndiv1, b.tiles[1], &g->scan_ctr[1], &g->err, 0,
+                                   s->blocks_scan));
+    RUN("apo_compact", 2, launch_apoptosis_compact(st, b, A, B, g, s->blocks_stream));
+    s->attr_cur ^= 1;
+    A = b.attr[s->attr_cur];
+    B = b.attr[s->attr_cur ^ 1];
+    s->bounds_fresh = false;
+  }
   if (s->growth) {
     RUN("grow", 1, launch_grow(st, b, A, g, p.growth_volume, p.division_volume, s->blocks_stream));
     CK(cudaMemsetAsync(b.tiles[1], 0, sizeof(unsigned long long) * scan_tiles_for(s->capacity + 1), st));
     RUN("scan_div", 1, launch_scan(st, b.flag, b.drank, &g->ndiv1, b.tiles[1], &g->scan_ctr[1], &g->err, 0,
                                    s->blocks_scan));
-    const uint2 key = make_uint2((unsigned)(p.seed & 0xFFFFFFFFull), p.run_id);
-    RUN("divide", 1, launch_divide(st, b, A, g, p.division_offset_frac, key, (unsigned)s->capacity,
+    RUN("divide", 1, launch_divide(st, b, A, g, p.division_offset_frac, pkey, (unsigned)s->capacity,
                                    s->blocks_stream));
     s->bounds_fresh = false;
   }
@@ -526,6 +544,11 @@ int enqueue_mech_step(bdm_sim* s) {
     RUN(s->mixed ? "force_mixed" : "force_fp64", 1, launch_force(st, b, B, g, s->mc, s->mixed, s->blocks_force));
     s->bounds_fresh = !s->growth;
     s->attr_cur ^= 1;
+    if (p.brownian_sigma > 0.0) {  // R13: after the capped update; the fused bounds are then stale
+      RUN("brownian", 1, launch_brownian(st, b, b.attr[s->attr_cur], g, p.brownian_sigma, pkey, !s->mixed,
+                                         s->blocks_stream));
+      s->bounds_fresh = false;
+    }
   }
   if (s->diffusion) {
     if (p.secretion != 0.0)

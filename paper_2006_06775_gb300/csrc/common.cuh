@@ -296,6 +296,12 @@ void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays&
                       int grid_blocks);
 int force_skin_blocks_per_sm(bool build);
 int list_build_blocks_per_sm();
+void launch_apoptosis_flags(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                            unsigned long long thr, uint2 key, int grid_blocks);
+void launch_apoptosis_compact(cudaStream_t s, const MechBuffers& b, const AgentArrays& src,
+                              const AgentArrays& dst, DevGrid* g, int grid_blocks);
+void launch_brownian(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                     double sigma, uint2 key, bool fp64, int grid_blocks);
 void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,
                         int grid_blocks);
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -1033,6 +1033,100 @@ __global__ void __launch_bounds__(kBlock) k_grow(float* __restrict__ diam,
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Oncology behaviours (readings R13, R14).  Apoptosis at step start: each agent dies with probability
+// p (Philox counter (id, step, 4, 0)); survivors keep their relative id order and take the dense ids
+// 0..m-1 (scan of the survival flags in id order), and move to the slot of their new id.  Brownian
+// migration after the capped mechanical update: sigma times standard normal deviates from the
+// Box-Muller transform of Philox words (counter (id, step, 3, 0)), evaluated in FP32 and added to
+// the FP64 centre.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_apo_flag(const unsigned* __restrict__ id,
+                                                     unsigned* __restrict__ flag, DevGrid* g,
+                                                     unsigned long long thr, uint2 key) {
+  const unsigned n = g->n;
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    g->ndiv1 = n + 1;
+    g->scan_ctr[1] = 0;
+    flag[n] = 0u;
+  }
+  const unsigned step = (unsigned)g->step;
+  for (unsigned k = tid; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned myid = id[k];
+    const uint4 w = philox10(make_uint4(myid, step, 4u, 0u), key);
+    flag[myid] = (unsigned long long)w.x >= thr ? 1u : 0u;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_apo_compact(
+    const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+    AgentArrays src, double* __restrict__ ox, double* __restrict__ oy, double* __restrict__ oz,
+    AgentArrays dst, const unsigned* __restrict__ flag, const unsigned* __restrict__ drank,
+    DevGrid* g) {
+  const unsigned n_old = g->ndiv1 - 1;
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (unsigned k = tid; k < n_old; k += gridDim.x * blockDim.x) {
+    const unsigned myid = src.id[k];
+    if (!flag[myid]) continue;
+    const unsigned m = drank[myid];
+    ox[m] = x[k];
+    oy[m] = y[k];
+    oz[m] = z[k];
+    dst.diam[m] = src.diam[k];
+    dst.id[m] = m;
+    if (src.vol) dst.vol[m] = src.vol[k];
+  }
+  if (tid == 0) g->n = drank[n_old];
+}
+
+__global__ void __launch_bounds__(kBlock) k_apo_copy(const double* __restrict__ x,
+                                                     const double* __restrict__ y,
+                                                     const double* __restrict__ z,
+                                                     double* __restrict__ ox, double* __restrict__ oy,
+                                                     double* __restrict__ oz, const DevGrid* g) {
+  const unsigned n = g->n;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    ox[k] = x[k];
+    oy[k] = y[k];
+    oz[k] = z[k];
+  }
+}
+
+// FP64: the deviates in double precision, in the oracle's expressions (the FP64 check path keeps
+// its positions within 1e-9 relative); mixed precision: in FP32.
+template <bool FP64>
+__global__ void __launch_bounds__(kBlock) k_brownian(double* __restrict__ x, double* __restrict__ y,
+                                                     double* __restrict__ z,
+                                                     const unsigned* __restrict__ id,
+                                                     const DevGrid* g, double sigma, uint2 key) {
+  const unsigned n = g->nbox ? g->n : 0u;
+  const unsigned step = (unsigned)g->step;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint4 w = philox10(make_uint4(id[k], step, 3u, 0u), key);
+    if constexpr (FP64) {
+      const double u = ((double)w.x + 1.0) * 0x1p-32, v = (double)w.y * 0x1p-32;
+      const double u2 = ((double)w.z + 1.0) * 0x1p-32, v2 = (double)w.w * 0x1p-32;
+      const double r = sqrt(-2.0 * log(u)), r2 = sqrt(-2.0 * log(u2));
+      const double pi2 = 2.0 * 3.141592653589793;
+      x[k] = x[k] + sigma * (r * cos(pi2 * v));
+      y[k] = y[k] + sigma * (r * sin(pi2 * v));
+      z[k] = z[k] + sigma * (r2 * cos(pi2 * v2));
+    } else {
+      const float u = ((float)w.x + 1.0f) * 0x1p-32f, v = (float)w.y * 0x1p-32f;
+      const float u2 = ((float)w.z + 1.0f) * 0x1p-32f, v2 = (float)w.w * 0x1p-32f;
+      const float r = sqrtf(-2.0f * logf(u)), r2 = sqrtf(-2.0f * logf(u2));
+      float sn, cs;
+      sincospif(2.0f * v, &sn, &cs);
+      const float cs2 = cospif(2.0f * v2);
+      const float sg = (float)sigma;
+      x[k] = __dadd_rn(x[k], (double)(sg * (r * cs)));
+      y[k] = __dadd_rn(y[k], (double)(sg * (r * sn)));
+      z[k] = __dadd_rn(z[k], (double)(sg * (r2 * cs2)));
+    }
+  }
+}
+
 // Division (R7 ii, iv): the m-th divider in id order gets daughter id/slot n_old + m.
 __global__ void __launch_bounds__(kBlock) k_divide(double* __restrict__ x, double* __restrict__ y,
                                                    double* __restrict__ z, float* __restrict__ diam,
@@ -1223,6 +1317,25 @@ int force_skin_blocks_per_sm(bool build) {
   if (build) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_force_skin<true>, kFT, 0);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_force_skin<false>, kFT, 0);
   return a > 0 ? a : 1;
+}
+
+void launch_apoptosis_flags(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                            unsigned long long thr, uint2 key, int grid_blocks) {
+  k_apo_flag<<<grid_blocks, kBlock, 0, s>>>(attr.id, b.flag, g, thr, key);
+}
+
+void launch_apoptosis_compact(cudaStream_t s, const MechBuffers& b, const AgentArrays& src,
+                              const AgentArrays& dst, DevGrid* g, int grid_blocks) {
+  k_apo_compact<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, src, b.sorted.x, b.sorted.y,
+                                               b.sorted.z, dst, b.flag, b.drank, g);
+  k_apo_copy<<<grid_blocks, kBlock, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, b.pos.x, b.pos.y,
+                                            b.pos.z, g);
+}
+
+void launch_brownian(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
+                     double sigma, uint2 key, bool fp64, int grid_blocks) {
+  if (fp64) k_brownian<true><<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, attr.id, g, sigma, key);
+  else k_brownian<false><<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, attr.id, g, sigma, key);
 }
 
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
