@@ -4,12 +4,12 @@ A plain, slow, obviously correct restatement of what one simulation step compute
 tests, by ``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``.  The product
 library never imports or links it and shares no code with it.  Each function cites the passage of
 BioDynaMo (arXiv 2006.06775) it follows, or the reading of the paper that fills a gap (readings
-R1-R14 are listed with their justification in the design notes at the repository root).
+R1-R15 are listed with their justification in the design notes at the repository root).
 
 Functions without an independent pin: the daughter offset distance and the division axis law (R7)
 are readings the paper does not fix; their tests check internal consistency only (parity unpinned).
-The oncology behaviours (Brownian migration R13, apoptosis R14) are readings too: the paper names
-them but prints neither law nor rate.  Their tests pin distributional facts (standard normal
+The oncology behaviours (Brownian migration R13, apoptosis R14) and chemotaxis (R15) are readings
+too: the paper names them but prints neither law nor rate.  Their tests pin distributional facts (standard normal
 deviates, binomial survival, order kept), not the paper's parameters.
 """
 import ctypes
@@ -58,6 +58,8 @@ def lib():
         L.orc_apoptosis.restype = ctypes.c_size_t
         L.orc_brownian.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, ctypes.c_double,
                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        L.orc_chemotaxis.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                     _f64p, _i64p, _f64p, ctypes.c_double, ctypes.c_double]
         L.orc_secrete.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, _f64p, _i64p, _f64p,
                                   ctypes.c_double, ctypes.c_double]
         L.orc_ftcs.argtypes = [_i64p, _f64p, _f64p, ctypes.c_double, ctypes.c_double]
@@ -173,6 +175,17 @@ def brownian(x, y, z, sigma, seed, run, step):
     x, y, z = _f64(x).copy(), _f64(y).copy(), _f64(z).copy()
     lib().orc_brownian(len(x), x, y, z, float(sigma), seed & 0xFFFFFFFF, run & 0xFFFFFFFF,
                        step & 0xFFFFFFFF)
+    return x, y, z
+
+
+def chemotaxis(x, y, z, sx, sy, sz, grid_values, origin, voxel, chi):
+    """Chemotaxis after the update (reading R15): returns x, y, z moved by chi * grad c, the grid
+    gradient at the voxel of the step-start centres (sx, sy, sz); grid shape (nz, ny, nx)."""
+    nz, ny, nx = grid_values.shape
+    x, y, z = _f64(x).copy(), _f64(y).copy(), _f64(z).copy()
+    lib().orc_chemotaxis(len(x), x, y, z, _f64(sx), _f64(sy), _f64(sz),
+                         np.ascontiguousarray(grid_values, np.float64).reshape(-1),
+                         np.array([nx, ny, nz], np.int64), _f64(origin), float(voxel), float(chi))
     return x, y, z
 
 
@@ -312,6 +325,7 @@ class OracleSim:
             self.diameter, self.volume = r["diameter"], r["volume"]
             self.n = len(self.x)
         if self.n:
+            x0, y0, z0 = self.x, self.y, self.z
             r = mech_step(self.x, self.y, self.z, self.diameter, p["dt"], p["repulsion"],
                           p["attraction"], p["max_displacement"], p.get("interaction_radius", 0.0),
                           p.get("box_length", 0.0))
@@ -322,6 +336,9 @@ class OracleSim:
                 self.x, self.y, self.z = brownian(self.x, self.y, self.z, p["brownian_sigma"],
                                                   p.get("seed", 0), p.get("run_id", 0),
                                                   self.step_index)
+            if p.get("chemotaxis", 0.0) and self.grid is not None:
+                self.x, self.y, self.z = chemotaxis(self.x, self.y, self.z, x0, y0, z0, self.grid,
+                                                    p["grid_origin"], p["voxel"], p["chemotaxis"])
         if p.get("diffusion_enabled"):
             if p.get("secretion", 0.0):
                 secrete(self.x, self.y, self.z, self.grid, p["grid_origin"], p["voxel"],

@@ -376,6 +376,39 @@ void orc_secrete(size_t n, const double* x, const double* y, const double* z, do
 }
 
 /* ------------------------------------------------------------------------------------------------
+ * Chemotaxis (paper Sec. "Simulation concepts": chemotaxis is an agent behaviour that reads the
+ * extracellular substance; its law is not printed).  Reading R15: after the mechanical update (and
+ * migration) every agent moves by chi * grad c, the gradient of the grid as it stood at the start of
+ * the step at the voxel of the agent's step-start centre (voxel as in R8).  Per axis: central
+ * difference (c[v+1] - c[v-1]) / (2h) inside, one-sided (c[v+1] - c[v]) / h or (c[v] - c[v-1]) / h at
+ * a wall, 0 along an axis of one voxel.
+ * ------------------------------------------------------------------------------------------------ */
+static double grid_derivative(const double* g, const int64_t dims[3], int64_t a, int64_t b,
+                              int64_t c, int axis, double h) {
+  const int64_t idx[3] = {a, b, c};
+  const int64_t n = dims[axis], v = idx[axis];
+  const int64_t stride = axis == 0 ? 1 : (axis == 1 ? dims[0] : dims[0] * dims[1]);
+  const int64_t at = a + dims[0] * (b + dims[1] * c);
+  if (n < 2) return 0.0;
+  if (v == 0) return (g[at + stride] - g[at]) / h;
+  if (v == n - 1) return (g[at] - g[at - stride]) / h;
+  return (g[at + stride] - g[at - stride]) / (2.0 * h);
+}
+
+void orc_chemotaxis(size_t n, double* x, double* y, double* z, const double* sx, const double* sy,
+                    const double* sz, const double* grid, const int64_t dims[3],
+                    const double origin[3], double h, double chi) {
+  for (size_t i = 0; i < n; ++i) {
+    const int64_t a = voxel_of(sx[i], origin[0], h, dims[0]);
+    const int64_t b = voxel_of(sy[i], origin[1], h, dims[1]);
+    const int64_t c = voxel_of(sz[i], origin[2], h, dims[2]);
+    x[i] = x[i] + chi * grid_derivative(grid, dims, a, b, c, 0, h);
+    y[i] = y[i] + chi * grid_derivative(grid, dims, a, b, c, 1, h);
+    z[i] = z[i] + chi * grid_derivative(grid, dims, a, b, c, 2, h);
+  }
+}
+
+/* ------------------------------------------------------------------------------------------------
  * Diffusion of an extracellular substance (paper Sec. "Simulation concepts": standalone operation,
  * once per step).  Reading R9: explicit forward-time centred-space 7-point update,
  *   u'_v = u_v + lambda * sum_{6 faces} (u_nb - u_v) - mu_dt * u_v,  lambda = D dt / h^2,

@@ -67,6 +67,10 @@ size_t orc_apoptosis(size_t n, double* x, double* y, double* z, float* diam, dou
 /* Brownian migration after the mechanical update (reading R13). */
 void orc_brownian(size_t n, double* x, double* y, double* z, double sigma, uint32_t seed_lo,
                   uint32_t run, uint32_t step);
+/* Chemotaxis after the update (reading R15): x += chi * grad c at the step-start voxel. */
+void orc_chemotaxis(size_t n, double* x, double* y, double* z, const double* sx, const double* sy,
+                    const double* sz, const double* grid, const int64_t dims[3],
+                    const double origin[3], double h, double chi);
 
 /* Secretion (reading R8): each agent adds q to the voxel that holds its centre (clamped). */
 void orc_secrete(size_t n, const double* x, const double* y, const double* z, double* grid,

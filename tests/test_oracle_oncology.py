@@ -69,3 +69,41 @@ def test_apoptosis_in_the_step_survival_follows_the_power_law():
     m = sim.get_state()["n"]
     q = (1.0 - p) ** 6
     assert abs(m / 20_000 - q) < 5.0 * math.sqrt(q * (1.0 - q) / 20_000)
+
+
+def _voxel_centres(n, h, o):
+    return o + h * (np.arange(n) + 0.5)
+
+
+def test_chemotaxis_follows_a_linear_field_exactly():
+    """On c = a.x + b the central and one-sided differences are exact: every agent, inside or at a
+    wall, moves by chi * a; a constant field moves nobody."""
+    nx, ny, nz, h, o = 7, 5, 4, 2.0, (-3.0, 1.0, 0.5)
+    a = np.array([0.25, -0.5, 1.5])
+    zc, yc, xc = np.meshgrid(_voxel_centres(nz, h, o[2]), _voxel_centres(ny, h, o[1]),
+                             _voxel_centres(nx, h, o[0]), indexing="ij")
+    grid = a[0] * xc + a[1] * yc + a[2] * zc + 3.0
+    g = synth.rng(14)
+    n = 500
+    sx = g.uniform(o[0] - 1.0, o[0] + nx * h + 1.0, n)  # some outside: clamped to the wall voxels
+    sy = g.uniform(o[1], o[1] + ny * h, n)
+    sz = g.uniform(o[2], o[2] + nz * h, n)
+    chi = 0.7
+    x, y, z = oracle.chemotaxis(sx, sy, sz, sx, sy, sz, grid, o, h, chi)
+    for got, start, ak in ((x, sx, a[0]), (y, sy, a[1]), (z, sz, a[2])):
+        assert np.allclose(got - start, chi * ak, rtol=0, atol=1e-12)
+    x, y, z = oracle.chemotaxis(sx, sy, sz, sx, sy, sz, np.full_like(grid, 2.0), o, h, chi)
+    assert np.array_equal(x, sx) and np.array_equal(y, sy) and np.array_equal(z, sz)
+
+
+def test_chemotaxis_moves_up_a_parabola():
+    """c = x^2 along x: inside, the central difference equals the derivative 2 x at the voxel
+    centre, and agents move towards higher concentration."""
+    nx, h, o = 9, 1.0, (0.0, 0.0, 0.0)
+    xc = _voxel_centres(nx, h, 0.0)
+    grid = np.broadcast_to((xc - 4.5) ** 2, (1, 1, nx)).copy()
+    sx = xc[1:-1].copy()
+    zero = np.zeros_like(sx)
+    x, _, _ = oracle.chemotaxis(sx, zero, zero, sx, zero, zero, grid, o, h, 1.0)
+    assert np.allclose(x - sx, 2.0 * (sx - 4.5), atol=1e-12)
+    assert np.all(np.sign(x - sx) == np.sign(sx - 4.5))
