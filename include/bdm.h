@@ -118,6 +118,9 @@ typedef struct bdm_params {
                                     agent moves by sigma * N(0,1) per axis (um); 0 = off          */
   double p_apoptosis;            /* each agent dies at the start of a step with this probability;
                                     survivors keep their order and take dense ids; 0 = off       */
+  double chemotaxis;             /* chi (reading R15, needs the substance grid): after the update
+                                    every agent moves by chi * grad c at its step-start voxel of
+                                    the step-start grid (um per unit of c per um); 0 = off        */
   /* Device plumbing. */
   void* stream;                  /* cudaStream_t, NULL = a stream the handle creates              */
   void* (*alloc)(size_t bytes, void* user); /* optional device allocator                         */

@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("capacity", ctypes.c_uint64), ("box_capacity", ctypes.c_uint64),
         ("skip_stationary", ctypes.c_int32), ("reserved4", ctypes.c_int32),
         ("brownian_sigma", ctypes.c_double), ("p_apoptosis", ctypes.c_double),
+        ("chemotaxis", ctypes.c_double),
         ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
     ]
@@ -150,7 +151,7 @@ def make_params(d: dict) -> Params:
     for name in ("dt", "repulsion", "attraction", "max_displacement", "interaction_radius",
                  "box_length", "skin", "growth_volume", "division_volume", "division_offset_frac", "voxel",
                  "diffusion_coeff", "decay", "dt_diffusion", "secretion", "sir_domain", "sir_radius",
-                 "sir_step", "p_infect", "p_recover", "brownian_sigma", "p_apoptosis"):
+                 "sir_step", "p_infect", "p_recover", "brownian_sigma", "p_apoptosis", "chemotaxis"):
         if name in d:
             setattr(p, name, float(d[name]))
     for name in ("growth_enabled", "force_variant", "diffusion_enabled", "sir_boxes", "skip_stationary"):

@@ -226,10 +226,13 @@ int check_params(bdm_sim* s, const bdm_params* p) {
       return fail(s, BDM_EINVAL, "brownian_sigma must be finite and >= 0");
     if (!(p->p_apoptosis >= 0.0 && p->p_apoptosis <= 1.0))
       return fail(s, BDM_EINVAL, "p_apoptosis must be in [0, 1]");
+    if (!std::isfinite(p->chemotaxis)) return fail(s, BDM_EINVAL, "chemotaxis must be finite");
+    if (p->chemotaxis != 0.0 && !p->diffusion_enabled)
+      return fail(s, BDM_EINVAL, "chemotaxis needs the substance grid (diffusion_enabled)");
     if (p->skin > 0.0 && (p->precision != BDM_MIXED || p->growth_enabled || p->force_variant != 0 ||
-                          p->brownian_sigma > 0.0 || p->p_apoptosis > 0.0))
+                          p->brownian_sigma > 0.0 || p->p_apoptosis > 0.0 || p->chemotaxis != 0.0))
       return fail(s, BDM_EINVAL, "a neighbour-list skin needs mixed precision, force_variant 0 and no "
-                                 "growth, apoptosis or Brownian migration");
+                                 "growth, apoptosis, Brownian migration or chemotaxis");
     if (p->growth_enabled) {
       if (!(p->growth_volume >= 0.0) || !(p->division_volume > 0.0) ||
           !(p->division_offset_frac >= 0.0))
@@ -547,6 +550,11 @@ int enqueue_mech_step(bdm_sim* s) {
     if (p.brownian_sigma > 0.0) {  // R13: after the capped update; the fused bounds are then stale
       RUN("brownian", 1, launch_brownian(st, b, b.attr[s->attr_cur], g, p.brownian_sigma, pkey, !s->mixed,
                                          s->blocks_stream));
+      s->bounds_fresh = false;
+    }
+    if (p.chemotaxis != 0.0 && s->diffusion) {  // R15: the step-start grid, before secretion
+      RUN("chemotaxis", 1, launch_chemotaxis(st, b, g, s->grid[s->grid_cur], s->gdims, p.grid_origin,
+                                             p.voxel, p.chemotaxis, s->blocks_stream));
       s->bounds_fresh = false;
     }
   }

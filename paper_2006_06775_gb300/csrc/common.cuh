@@ -302,6 +302,9 @@ void launch_apoptosis_compact(cudaStream_t s, const MechBuffers& b, const AgentA
                               const AgentArrays& dst, DevGrid* g, int grid_blocks);
 void launch_brownian(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                      double sigma, uint2 key, bool fp64, int grid_blocks);
+void launch_chemotaxis(cudaStream_t s, const MechBuffers& b, DevGrid* g, const float* grid,
+                       const int dims[3], const double origin[3], double h, double chi,
+                       int grid_blocks);
 void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,
                         int grid_blocks);
 void launch_grow(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,

@@ -1190,6 +1190,38 @@ __device__ __forceinline__ int voxel_of(double v, double o, double h, int n) {
   return (int)f;
 }
 
+// Chemotaxis (reading R15): x += chi * grad c, the gradient of the step-start grid at the voxel of
+// the step-start centre (central differences inside, one-sided at walls, 0 along a one-voxel axis),
+// in FP64 in the oracle's expressions.
+__device__ __forceinline__ double grid_derivative(const float* __restrict__ u, int a, int b, int c,
+                                                  int nx, int ny, int nz, int axis, double h) {
+  const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+  const int v = axis == 0 ? a : (axis == 1 ? b : c);
+  const size_t stride = axis == 0 ? 1u : (axis == 1 ? (size_t)nx : (size_t)nx * (size_t)ny);
+  const size_t at = (size_t)a + (size_t)nx * ((size_t)b + (size_t)ny * (size_t)c);
+  if (n < 2) return 0.0;
+  if (v == 0) return ((double)u[at + stride] - (double)u[at]) / h;
+  if (v == n - 1) return ((double)u[at] - (double)u[at - stride]) / h;
+  return ((double)u[at + stride] - (double)u[at - stride]) / (2.0 * h);
+}
+
+__global__ void __launch_bounds__(kBlock) k_chemotaxis(double* __restrict__ x, double* __restrict__ y,
+                                                       double* __restrict__ z,
+                                                       const double* __restrict__ sx,
+                                                       const double* __restrict__ sy,
+                                                       const double* __restrict__ sz,
+                                                       const float* __restrict__ grid, const DevGrid* g,
+                                                       int nx, int ny, int nz, double ox, double oy,
+                                                       double oz, double h, double chi) {
+  const unsigned n = g->nbox ? g->n : 0u;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int a = voxel_of(sx[k], ox, h, nx), b = voxel_of(sy[k], oy, h, ny), c = voxel_of(sz[k], oz, h, nz);
+    x[k] = x[k] + chi * grid_derivative(grid, a, b, c, nx, ny, nz, 0, h);
+    y[k] = y[k] + chi * grid_derivative(grid, a, b, c, nx, ny, nz, 1, h);
+    z[k] = z[k] + chi * grid_derivative(grid, a, b, c, nx, ny, nz, 2, h);
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_secrete(const double* __restrict__ x,
                                                     const double* __restrict__ y,
                                                     const double* __restrict__ z,
@@ -1347,6 +1379,14 @@ void launch_divide(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr
                    double offset_frac, uint2 key, unsigned capacity, int grid_blocks) {
   k_divide<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, attr.diam, attr.id, attr.vol,
                                           b.flag, b.drank, g, offset_frac, key, capacity);
+}
+
+void launch_chemotaxis(cudaStream_t s, const MechBuffers& b, DevGrid* g, const float* grid,
+                       const int dims[3], const double origin[3], double h, double chi,
+                       int grid_blocks) {
+  k_chemotaxis<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, b.sorted.x, b.sorted.y,
+                                              b.sorted.z, grid, g, dims[0], dims[1], dims[2],
+                                              origin[0], origin[1], origin[2], h, chi);
 }
 
 void launch_secrete(cudaStream_t s, const MechBuffers& b, DevGrid* g, float* grid,

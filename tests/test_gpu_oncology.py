@@ -67,3 +67,39 @@ def test_oncology_parameters_are_checked():
                 dict(growth_enabled=0, skin=2.0, interaction_radius=14.0)):
         with pytest.raises(bdm.BdmError):
             bdm.Sim(dict(params, **bad))
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 2e-4), ("fp64", 1e-8)])
+def test_chemotaxis_teacher_forced(precision, tol):
+    """Secreting spheroid on the co-stepped grid, agents following the gradient (reading R15): from
+    the GPU's state and grid, one oracle step gives the same agents, counts and grid assignment, and
+    positions within the path's tolerance."""
+    params, inp = synth.spheroid(seed=5, grid_n=64)
+    params = dict(params, precision=precision, capacity=1 << 15, chemotaxis=50.0,
+                  grid_origin=(-320.0, -320.0, -320.0))
+    sim = bdm.Sim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    sim.step(3)  # some substance first
+    prev = sim.get_state()
+    moved = 0.0
+    for k in range(3, 11):
+        sim.step(1)
+        got = sim.get_state()
+        ref = oracle.OracleSim(dict(params, first_step=k))
+        ref.add_agents(prev["x"], prev["y"], prev["z"], prev["diameter"], prev["volume"])
+        ref.set_grid(prev["grid"])
+        ref.step(1)
+        want = ref.get_state()
+        assert got["n"] == want["n"], k
+        for f in ("diameter", "volume", "neighbour_count", "box_id"):
+            assert np.array_equal(got[f], want[f]), (k, f)
+        for a in ("x", "y", "z"):
+            assert np.max(np.abs(got[a] - want[a])) < tol, (k, a)
+        no_chemo = oracle.OracleSim(dict(params, first_step=k, chemotaxis=0.0))
+        no_chemo.add_agents(prev["x"], prev["y"], prev["z"], prev["diameter"], prev["volume"])
+        no_chemo.set_grid(prev["grid"])
+        no_chemo.step(1)
+        moved = max(moved, float(np.max(np.abs(want["x"] - no_chemo.get_state()["x"]))))
+        prev = got
+    assert moved > 1e-3  # the gradient term is not negligible in this test
+    sim.close()
