@@ -4,13 +4,16 @@ A plain, slow, obviously correct restatement of what one simulation step compute
 tests, by ``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``.  The product
 library never imports or links it and shares no code with it.  Each function cites the passage of
 BioDynaMo (arXiv 2006.06775) it follows, or the reading of the paper that fills a gap (readings
-R1-R15 are listed with their justification in the design notes at the repository root).
+R1-R20 are listed with their justification in the design notes at the repository root).
 
 Functions without an independent pin: the daughter offset distance and the division axis law (R7)
 are readings the paper does not fix; their tests check internal consistency only (parity unpinned).
 The oncology behaviours (Brownian migration R13, apoptosis R14) and chemotaxis (R15) are readings
 too: the paper names them but prints neither law nor rate.  Their tests pin distributional facts (standard normal
-deviates, binomial survival, order kept), not the paper's parameters.
+deviates, binomial survival, order kept), not the paper's parameters.  Neurite mechanics (R16-R20)
+follows a force law the paper does not print (it names the Cortex3D model): its tests pin the
+geometry (closest points against brute-force minimisation), the spring and lever split against
+closed forms, and the conservation of the total force; the law itself is parity unpinned.
 """
 import ctypes
 import math
@@ -34,6 +37,12 @@ class MechParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("k_rep", ctypes.c_double), ("gamma_att", ctypes.c_double),
                 ("max_disp", ctypes.c_double), ("interaction_radius", ctypes.c_double),
                 ("box_length", ctypes.c_double)]
+
+
+class NeuriteParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("k_rep", ctypes.c_double), ("gamma_att", ctypes.c_double),
+                ("max_disp", ctypes.c_double), ("k_spring", ctypes.c_double),
+                ("interaction_radius", ctypes.c_double)]
 
 
 def lib():
@@ -68,6 +77,13 @@ def lib():
                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, _i32p, _i32p, _i32p, _u8p, _u32p, _u32p, _u32p]
+        L.orc_segment_closest.argtypes = [_f64p, _f64p, _f64p, _f64p,
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.orc_neurite_step.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, _f64p, _f64p, _i32p,
+                                       _f64p, _f64p, _f64p, ctypes.POINTER(NeuriteParams), _f64p,
+                                       _f64p, _f64p, _u32p, ctypes.POINTER(ctypes.c_double),
+                                       _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -140,6 +156,36 @@ def mech_step(x, y, z, diam, dt, repulsion, attraction, max_displacement, intera
     if want_force:
         res["force"] = np.stack([out["fx"], out["fy"], out["fz"]], axis=1)
     return res
+
+
+# ------------------------------------------------------------------------------------------------
+# Neurite mechanics (paper Sec. "Neuroscience module"; readings R16-R20)
+# ------------------------------------------------------------------------------------------------
+def segment_closest(p0, u, q0, v):
+    """Parameters (s, t) in [0, 1]^2 of the closest points of segments p0 + s u and q0 + t v."""
+    s, t = ctypes.c_double(), ctypes.c_double()
+    lib().orc_segment_closest(_f64(p0), _f64(u), _f64(q0), _f64(v), ctypes.byref(s),
+                              ctypes.byref(t))
+    return s.value, t.value
+
+
+def neurite_step(x, y, z, diam, rest, mother, ox, oy, oz, dt, repulsion, attraction,
+                 max_displacement, spring, interaction_radius=0.0):
+    """One Jacobi step of neurite mechanics (brute force over all pairs).  Returns a dict of new
+    x, y, z, neighbour counts, the radius L and each agent's total force (n, 3)."""
+    n = len(x)
+    p = NeuriteParams(dt, repulsion, attraction, max_displacement, spring, interaction_radius)
+    out = {k: np.zeros(n) for k in ("x", "y", "z", "fx", "fy", "fz")}
+    nbr = np.zeros(n, np.uint32)
+    L = ctypes.c_double(0.0)
+    rc = lib().orc_neurite_step(n, _f64(x), _f64(y), _f64(z), _f64(diam), _f64(rest),
+                                np.ascontiguousarray(mother, dtype=np.int32), _f64(ox), _f64(oy),
+                                _f64(oz), ctypes.byref(p), out["x"], out["y"], out["z"], nbr,
+                                ctypes.byref(L), out["fx"], out["fy"], out["fz"])
+    if rc:
+        raise ValueError("orc_neurite_step rejected the input (%d)" % rc)
+    return {"x": out["x"], "y": out["y"], "z": out["z"], "neighbour_count": nbr, "L": L.value,
+            "force": np.stack([out["fx"], out["fy"], out["fz"]], axis=1)}
 
 
 def grow_divide(x, y, z, diam, vol, growth_volume, division_volume, offset_frac, seed, run, step):

@@ -547,3 +547,188 @@ int orc_sir_step(size_t n, const int32_t* X, const int32_t* Y, const int32_t* Z,
   free(key); free(start); free(order);
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Neurite mechanics (paper Sec. "Neuroscience module": neurite elements are cylinders, modelled as a
+ * spring with a point mass at the distal end, connected as a binary tree so that forces travel
+ * along the chain; Sec. "Simulation concepts": sphere or cylinder geometry).  The paper prints no
+ * force law for cylinders; readings R16-R20:
+ *   R16 agent a is a soma (mother[a] < 0; a sphere at p_a) or a neurite element (a cylinder from
+ *       the proximal point q_a = p_{mother[a]} + o_a to the distal point p_a), radius r_a = d_a / 2;
+ *   R17 spring: v = p_e - q_e, l = |v|, T = k_s (l - l0_e) / l0_e; the distal point takes -T v / l,
+ *       the mother +T v / l (nothing when l = 0);
+ *   R18 contact between the bodies of i and j (not excluded): closest points c_i, c_j (a soma's is
+ *       its centre; an element's lies on its axis at parameter s_i in [0, 1], 0 proximal), then the
+ *       sphere law of R3 between them: dv = c_i - c_j, d = |dv|, delta = (r_i + r_j) - d; when
+ *       delta > 0 and d > 0, f = (F / d) dv with F = k delta - gamma sqrt(rho delta).  A soma takes
+ *       f; an element takes s_i f at its distal point and passes (1 - s_i) f to its mother;
+ *   R19 excluded pairs (they share an end point): an element and its mother, an element and its
+ *       daughters, two elements with the same mother;
+ *   R20 neighbours: binning point b_a = p_a (soma) or 0.5 (q_a + p_a) (element); extent e_a = d_a or
+ *       l_a + d_a; radius L = max_a e_a (or a larger fixed value); a neighbour of i is j != i with
+ *       |b_i - b_j|^2 < L^2.  Every contact pair is a neighbour pair: |b_i - b_j| <= l_i/2 + l_j/2 +
+ *       |c_i - c_j| < e_i/2 + e_j/2 <= L.
+ *   update (R4): D = dt (own share + sum over daughters of what they pass up), capped, p += D.
+ * This oracle takes every pair (brute force over all j), so it does not depend on any grid.
+ * ------------------------------------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) {
+  return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
+
+/* Closest points of segments P(s) = P0 + s u and Q(t) = Q0 + t v, s, t in [0, 1] (a zero-length
+ * segment is a point).  Minimises |P(s) - Q(t)|^2, a convex quadratic on the unit square: the
+ * minimiser of the infinite lines clamped in s, then t optimal for that s, and if t had to be clamped
+ * s optimal for the clamped t (Ericson, Real-Time Collision Detection, Sec. 5.1.9). */
+void orc_segment_closest(const double P0[3], const double u[3], const double Q0[3],
+                         const double v[3], double* s_out, double* t_out) {
+  double w[3] = {P0[0] - Q0[0], P0[1] - Q0[1], P0[2] - Q0[2]};
+  double A = dot3(u, u), B = dot3(u, v), C = dot3(v, v), D = dot3(u, w), E = dot3(v, w);
+  double s, t;
+  if (A <= 0.0 && C <= 0.0) {
+    s = 0.0; t = 0.0;
+  } else if (A <= 0.0) {
+    s = 0.0; t = clamp01(E / C);
+  } else if (C <= 0.0) {
+    t = 0.0; s = clamp01(-D / A);
+  } else {
+    double den = A * C - B * B;
+    s = den > 1e-12 * (A * C) ? clamp01((B * E - C * D) / den) : 0.0;
+    t = (B * s + E) / C;
+    if (t < 0.0) {
+      t = 0.0; s = clamp01(-D / A);
+    } else if (t > 1.0) {
+      t = 1.0; s = clamp01((B - D) / A);
+    }
+  }
+  *s_out = s;
+  *t_out = t;
+}
+
+typedef struct {
+  double p[3], q[3], ax[3];  /* distal point, proximal point, axis p - q (zero for a soma) */
+  double r, len;             /* radius, axis length                                       */
+  int64_t mother;
+} orc_body_t;
+
+static void neurite_body(size_t a, const double* x, const double* y, const double* z,
+                         const double* diam, const int32_t* mother, const double* ox,
+                         const double* oy, const double* oz, orc_body_t* B) {
+  B->p[0] = x[a]; B->p[1] = y[a]; B->p[2] = z[a];
+  B->r = 0.5 * diam[a];
+  B->mother = mother[a];
+  if (mother[a] < 0) {
+    for (int k = 0; k < 3; ++k) { B->q[k] = B->p[k]; B->ax[k] = 0.0; }
+    B->len = 0.0;
+  } else {
+    size_t m = (size_t)mother[a];
+    B->q[0] = x[m] + ox[a]; B->q[1] = y[m] + oy[a]; B->q[2] = z[m] + oz[a];
+    for (int k = 0; k < 3; ++k) B->ax[k] = B->p[k] - B->q[k];
+    B->len = sqrt(dot3(B->ax, B->ax));
+  }
+}
+
+int orc_neurite_step(size_t n, const double* x, const double* y, const double* z,
+                     const double* diam, const double* rest, const int32_t* mother,
+                     const double* ox, const double* oy, const double* oz,
+                     const orc_neurite_params* p, double* nx, double* ny, double* nz,
+                     uint32_t* nbr, double* L_out, double* fx, double* fy, double* fz) {
+  if (n == 0) return 0;
+  for (size_t a = 0; a < n; ++a) {
+    if (mother[a] >= (int64_t)a || mother[a] < -1) return -1;
+    if (!(diam[a] > 0.0)) return -1;
+    if (mother[a] >= 0 && !(rest[a] > 0.0)) return -1;
+  }
+  orc_body_t* B = (orc_body_t*)malloc(n * sizeof(orc_body_t));
+  double* bin = (double*)malloc(3 * n * sizeof(double));
+  double* up = (double*)calloc(3 * n, sizeof(double));   /* what each element passes to its mother */
+  double* own = (double*)calloc(3 * n, sizeof(double));  /* what each agent keeps                  */
+  if (!B || !bin || !up || !own) {
+    free(B); free(bin); free(up); free(own);
+    return -2;
+  }
+  double L = p->interaction_radius;
+  for (size_t a = 0; a < n; ++a) {
+    neurite_body(a, x, y, z, diam, mother, ox, oy, oz, &B[a]);
+    double e = B[a].len + diam[a];
+    if (e > L) L = e;
+    for (int k = 0; k < 3; ++k)
+      bin[3 * a + k] = mother[a] < 0 ? B[a].p[k] : 0.5 * (B[a].q[k] + B[a].p[k]);
+  }
+  const double L2 = L * L;
+  const double k = p->k_rep, gam = p->gamma_att;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+  for (long long ii = 0; ii < (long long)n; ++ii) {
+    size_t i = (size_t)ii;
+    const orc_body_t* bi = &B[i];
+    double keep[3] = {0.0, 0.0, 0.0}, pass[3] = {0.0, 0.0, 0.0};
+    uint32_t cnt = 0;
+    if (bi->mother >= 0 && bi->len > 0.0) {  /* R17 */
+      double T = p->k_spring * (bi->len - rest[i]) / rest[i];
+      for (int c = 0; c < 3; ++c) {
+        double f = T * (bi->ax[c] / bi->len);
+        keep[c] -= f;
+        pass[c] += f;
+      }
+    }
+    for (size_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const orc_body_t* bj = &B[j];
+      double db[3] = {bin[3 * i] - bin[3 * j], bin[3 * i + 1] - bin[3 * j + 1],
+                      bin[3 * i + 2] - bin[3 * j + 2]};
+      double d2 = db[0] * db[0] + db[1] * db[1];
+      d2 = d2 + db[2] * db[2];
+      if (d2 < L2) cnt++;
+      /* R19 */
+      if (bi->mother == (int64_t)j || bj->mother == (int64_t)i) continue;
+      if (bi->mother >= 0 && bi->mother == bj->mother) continue;
+      double s = 0.0, t = 0.0;
+      orc_segment_closest(bi->q, bi->ax, bj->q, bj->ax, &s, &t);
+      double dv[3];
+      for (int c = 0; c < 3; ++c) dv[c] = (bi->q[c] + s * bi->ax[c]) - (bj->q[c] + t * bj->ax[c]);
+      double d = sqrt(dot3(dv, dv));
+      double delta = (bi->r + bj->r) - d;
+      if (delta > 0.0 && d > 0.0) {
+        double rho = (bi->r * bj->r) / (bi->r + bj->r);
+        double F = k * delta - gam * sqrt(rho * delta);
+        for (int c = 0; c < 3; ++c) {
+          double f = (F / d) * dv[c];
+          if (bi->mother < 0) {
+            keep[c] += f;
+          } else {
+            keep[c] += s * f;
+            pass[c] += (1.0 - s) * f;
+          }
+        }
+      }
+    }
+    for (int c = 0; c < 3; ++c) { own[3 * i + c] = keep[c]; up[3 * i + c] = pass[c]; }
+    nbr[i] = cnt;
+  }
+  /* daughters pass their share to the mother, taken in ascending daughter id */
+  for (size_t a = 0; a < n; ++a) {
+    if (mother[a] < 0) continue;
+    size_t m = (size_t)mother[a];
+    for (int c = 0; c < 3; ++c) own[3 * m + c] += up[3 * a + c];
+  }
+  for (size_t a = 0; a < n; ++a) {
+    double S[3] = {own[3 * a], own[3 * a + 1], own[3 * a + 2]};
+    if (fx) { fx[a] = S[0]; fy[a] = S[1]; fz[a] = S[2]; }
+    double Dx = p->dt * S[0], Dy = p->dt * S[1], Dz = p->dt * S[2];
+    double norm = Dx * Dx + Dy * Dy;
+    norm = sqrt(norm + Dz * Dz);
+    if (norm > p->max_disp) {
+      double f = p->max_disp / norm;
+      Dx = Dx * f; Dy = Dy * f; Dz = Dz * f;
+    }
+    nx[a] = x[a] + Dx;
+    ny[a] = y[a] + Dy;
+    nz[a] = z[a] + Dz;
+  }
+  if (L_out) *L_out = L;
+  free(B); free(bin); free(up); free(own);
+  return 0;
+}

@@ -89,6 +89,24 @@ int orc_sir_step(size_t n, const int32_t* X, const int32_t* Y, const int32_t* Z,
                  uint32_t seed_lo, uint32_t run, uint32_t step, int32_t* nX, int32_t* nY,
                  int32_t* nZ, uint8_t* nst, uint32_t* ninf, uint32_t* box_id, uint32_t counts[3]);
 
+/* Neurite mechanics (readings R16-R20): somata (mother < 0, spheres) and neurite elements
+ * (cylinders from p_mother + o to p).  mother[a] < a for every element (a tree in creation order).
+ * Brute force over all pairs.  Writes new positions, neighbour counts (R20), the radius L used
+ * (L_out, may be NULL) and, when fx is not NULL, each agent's total force. */
+typedef struct {
+  double dt, k_rep, gamma_att, max_disp;
+  double k_spring;            /* spring constant of an element (R17)                  */
+  double interaction_radius;  /* lower bound of L; 0 = the largest extent (R20)       */
+} orc_neurite_params;
+
+void orc_segment_closest(const double P0[3], const double u[3], const double Q0[3],
+                         const double v[3], double* s_out, double* t_out);
+int orc_neurite_step(size_t n, const double* x, const double* y, const double* z,
+                     const double* diam, const double* rest, const int32_t* mother,
+                     const double* ox, const double* oy, const double* oz,
+                     const orc_neurite_params* p, double* nx, double* ny, double* nz,
+                     uint32_t* nbr, double* L_out, double* fx, double* fy, double* fz);
+
 /* Threads the OpenMP build uses (1 without OpenMP). */
 int orc_num_threads(void);
 

@@ -234,3 +234,85 @@ def served_sir(n: int, seed: int, density: float = 20_000 / 1000.0 ** 3, boxes_p
     params = dict(kind="sir", seed=seed, run_id=0, sir_domain=domain, sir_radius=6.0, sir_step=5.0,
                   sir_boxes=boxes_per_side or 0, p_infect=p_inf, p_recover=p_rec)
     return params, dict(x=x, y=y, z=z, sir_state=st)
+
+
+# ------------------------------------------------------------------------------------------------
+# Neuron forest (Sec. "Neuroscience use case": pyramidal cells with one apical and three basal
+# dendrites on a 10 um soma; branching probabilities 0.038 apical and 0.006 basal per step; apical
+# dendrites grow twice as fast; the large run holds 5000 cells and 9 million agents)
+# ------------------------------------------------------------------------------------------------
+NEURITE_DEFAULTS = dict(kind="neurite", dt=0.01, repulsion=2.0, attraction=1.0,
+                        max_displacement=3.0, spring=10.0, interaction_radius=0.0)
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def neuron_forest(n_neurons: int = 5000, n_agents: int = 9_000_000, side: float = 2000.0,
+                  seed: int = 6, soma_diameter: float = 10.0, stretch: float = 0.1,
+                  persistence: float = 0.35):
+    """Somata uniform in [0, side)^3, each with one apical and three basal dendrites grown as random
+    binary trees, one element per tip per generation, until the forest holds n_agents agents
+    (somata first, then elements generation by generation, so every mother precedes its daughters).
+    Element rest lengths: basal U[1.5, 2.5] um, apical U[3, 5] um; actual lengths are the rest length
+    times U[1 - stretch, 1 + stretch]; diameters taper from 1.5 (apical) / 1.2 (basal) by 0.5% per
+    generation down to 0.5 um.  A root element starts on the soma surface (offset r_soma * direction);
+    every other element starts at its mother's distal point (offset 0).  Directions follow a
+    persistent random walk; a branch point spawns two daughters deflected to either side."""
+    if n_agents < n_neurons:
+        raise ValueError("n_agents must cover the somata")
+    g = rng(seed, 9)
+    cx = g.uniform(0.0, side, n_neurons)
+    cy = g.uniform(0.0, side, n_neurons)
+    cz = g.uniform(0.0, side, n_neurons)
+    cols = {k: [a] for k, a in (("x", cx), ("y", cy), ("z", cz))}
+    cols["diameter"] = [np.full(n_neurons, soma_diameter)]
+    cols["rest"] = [np.zeros(n_neurons)]
+    cols["mother"] = [np.full(n_neurons, -1, np.int64)]
+    for k in ("ox", "oy", "oz"):
+        cols[k] = [np.zeros(n_neurons)]
+    # tips: one apical (kind 1) and three basal (kind 0) per soma
+    kind = np.tile(np.array([1, 0, 0, 0], np.int8), n_neurons)
+    soma = np.repeat(np.arange(n_neurons), 4)
+    d = g.normal(size=(4 * n_neurons, 3))
+    d[kind == 1] = d[kind == 1] * 0.2 + np.array([0.0, 0.0, 1.0])
+    d[kind == 0] = d[kind == 0] + np.array([0.0, 0.0, -0.5])
+    d = _unit(d)
+    r_s = 0.5 * soma_diameter
+    mother = soma.astype(np.int64)
+    base = np.stack([cx[soma], cy[soma], cz[soma]], 1)
+    off = r_s * d
+    prox = base + off
+    diam = np.where(kind == 1, 1.5, 1.2)
+    total = n_neurons
+    while total < n_agents:
+        take = min(len(mother), n_agents - total)
+        mother, prox, off, d, diam, kind = (mother[:take], prox[:take], off[:take], d[:take],
+                                            diam[:take], kind[:take])
+        d = _unit(d + persistence * g.normal(size=d.shape))
+        rest = np.where(kind == 1, g.uniform(3.0, 5.0, take), g.uniform(1.5, 2.5, take))
+        length = rest * g.uniform(1.0 - stretch, 1.0 + stretch, take)
+        dist = prox + d * length[:, None]
+        idx = np.arange(total, total + take)
+        for k, a in (("x", dist[:, 0]), ("y", dist[:, 1]), ("z", dist[:, 2]), ("diameter", diam),
+                     ("rest", rest), ("mother", mother), ("ox", off[:, 0]), ("oy", off[:, 1]),
+                     ("oz", off[:, 2])):
+            cols[k].append(a)
+        total += take
+        # next generation: every element continues; a branch point adds a second daughter
+        branch = g.uniform(size=take) < np.where(kind == 1, 0.038, 0.006)
+        perp = _unit(np.cross(d, g.normal(size=d.shape)))
+        d_next = np.where(branch[:, None], _unit(d + 0.6 * perp), d)
+        d_extra = _unit(d[branch] - 0.6 * perp[branch])
+        mother = np.concatenate([idx, idx[branch]])
+        prox = np.concatenate([dist, dist[branch]])
+        d = np.concatenate([d_next, d_extra])
+        dn = np.maximum(diam * 0.995, 0.5)
+        diam = np.concatenate([dn, dn[branch]])
+        kind = np.concatenate([kind, kind[branch]])
+        off = np.zeros_like(prox)
+    inp = {k: np.concatenate(v) for k, v in cols.items()}
+    inp["mother"] = inp["mother"].astype(np.int32)
+    params = dict(NEURITE_DEFAULTS, seed=seed)
+    return params, inp

@@ -1,0 +1,194 @@
+"""Oracle pins for neurite mechanics (readings R16-R20; paper Sec. "Neuroscience module").
+
+The closest-point geometry is checked against brute-force minimisation; the spring, the lever split
+of a contact force along a cylinder and the cylinder-cylinder contact against closed forms; a forest
+of somata alone against the sphere-mechanics oracle; and every forest against the conservation of
+the total force (contacts are equal and opposite, the split and the spring move force between agents
+without creating any), rotation invariance, and the neighbour definition via a k-d tree."""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+from scipy.spatial.transform import Rotation
+
+import oracle
+from paper_2006_06775_gb300 import synth
+
+K, GAM, DT, CAP, KS = 2.0, 1.0, 0.01, 3.0, 10.0
+
+
+def step(inp, **kw):
+    p = dict(dt=DT, repulsion=K, attraction=GAM, max_displacement=CAP, spring=KS)
+    p.update(kw)
+    return oracle.neurite_step(inp["x"], inp["y"], inp["z"], inp["diameter"], inp["rest"],
+                               inp["mother"], inp["ox"], inp["oy"], inp["oz"], p["dt"],
+                               p["repulsion"], p["attraction"], p["max_displacement"], p["spring"],
+                               p.get("interaction_radius", 0.0))
+
+
+def agents(rows):
+    """rows: (x, y, z, diameter, rest, mother, ox, oy, oz)"""
+    a = np.array(rows, dtype=np.float64).reshape(-1, 9)
+    inp = {k: np.ascontiguousarray(a[:, i]) for i, k in
+           enumerate(("x", "y", "z", "diameter", "rest", "mother", "ox", "oy", "oz"))}
+    inp["mother"] = inp["mother"].astype(np.int32)
+    return inp
+
+
+def contact_F(delta, r1, r2):
+    rho = r1 * r2 / (r1 + r2)
+    return K * delta - GAM * math.sqrt(rho * delta)
+
+
+def _brute_min(p0, u, q0, v, n=401):
+    s = np.linspace(0.0, 1.0, n)
+    P = p0[None, :] + s[:, None] * u[None, :]
+    Q = q0[None, :] + s[:, None] * v[None, :]
+    d = np.linalg.norm(P[:, None, :] - Q[None, :, :], axis=2)
+    i, j = np.unravel_index(np.argmin(d), d.shape)
+    # refine around the grid minimum
+    s2 = np.clip(np.linspace(s[i] - 2.0 / n, s[i] + 2.0 / n, 201), 0, 1)
+    t2 = np.clip(np.linspace(s[j] - 2.0 / n, s[j] + 2.0 / n, 201), 0, 1)
+    P = p0[None, :] + s2[:, None] * u[None, :]
+    Q = q0[None, :] + t2[:, None] * v[None, :]
+    return float(np.min(np.linalg.norm(P[:, None, :] - Q[None, :, :], axis=2)))
+
+
+def test_segment_closest_points_match_brute_force():
+    g = synth.rng(30)
+    cases = []
+    for _ in range(60):
+        cases.append((g.normal(size=3), g.normal(size=3), g.normal(size=3), g.normal(size=3)))
+    u = g.normal(size=3)
+    cases += [(np.zeros(3), u, np.array([0.3, 0.1, 0.2]), 0.5 * u),        # parallel
+              (np.zeros(3), u, 2.0 * u, u),                                # collinear, apart
+              (np.zeros(3), np.zeros(3), g.normal(size=3), g.normal(size=3)),  # point-segment
+              (g.normal(size=3), g.normal(size=3), np.ones(3), np.zeros(3)),   # segment-point
+              (np.zeros(3), np.zeros(3), np.ones(3), np.zeros(3))]         # point-point
+    for p0, u, q0, v in cases:
+        s, t = oracle.segment_closest(p0, u, q0, v)
+        assert 0.0 <= s <= 1.0 and 0.0 <= t <= 1.0
+        d = float(np.linalg.norm((p0 + s * u) - (q0 + t * v)))
+        assert d <= _brute_min(p0, u, q0, v) + 1e-9
+
+
+def test_segment_closest_crossing_closed_form():
+    # x axis segment [0, 4] and a segment along y through (1, *, 2): closest at s = 0.25, t = 0.5
+    s, t = oracle.segment_closest([0, 0, 0], [4, 0, 0], [1, -1, 2], [0, 2, 0])
+    assert s == 0.25 and t == 0.5
+
+
+def test_spring_closed_form_and_mother_exclusion():
+    """A soma and one root element stretched by 30 %: the element pulls the soma with T = k (l - l0)
+    / l0 along the axis and takes -T; the element overlaps its soma, but mother pairs do not touch."""
+    l0, l = 2.0, 2.6
+    inp = agents([(0, 0, 0, 10, 0, -1, 0, 0, 0),
+                  (5 + l, 0, 0, 1.0, l0, 0, 5, 0, 0)])
+    r = step(inp)
+    T = KS * (l - l0) / l0
+    assert np.allclose(r["force"][1], [-T, 0, 0], rtol=0, atol=1e-12)
+    assert np.allclose(r["force"][0], [T, 0, 0], rtol=0, atol=1e-12)
+    assert np.allclose(r["x"] - inp["x"], DT * np.array([T, -T]), atol=1e-14)
+    assert r["L"] == 10.0
+    assert list(r["neighbour_count"]) == [1, 1]
+
+
+def test_contact_force_is_split_by_the_lever_rule():
+    """A sphere touches an element at 30 % of its length: the sphere takes F along the normal, the
+    element's distal point s F = 0.3 F and its mother 0.7 F in the opposite direction."""
+    rs, re, h = 2.0, 0.5, 2.2
+    inp = agents([(-100, 0, 0, 10, 0, -1, 95, 0, 0),   # far soma, element 1's mother
+                  (10, 0, 0, 1.0, 15.0, 0, 95, 0, 0),   # element from (-5, 0, 0) to (10, 0, 0)
+                  (-0.5, 0, h, 2 * rs, 0, -1, 0, 0, 0)])  # sphere above x = -0.5: s = 0.3
+    r = step(inp)
+    F = contact_F(rs + re - h, re, rs)
+    assert np.allclose(r["force"][2], [0, 0, F], atol=1e-12)
+    assert np.allclose(r["force"][1], [0, 0, -0.3 * F], atol=1e-12)
+    assert np.allclose(r["force"][0], [0, 0, -0.7 * F], atol=1e-12)
+
+
+def test_crossing_cylinders_closed_form():
+    """Two elements crossing at right angles, axes 0.9 um apart along z, radii 0.5 and 0.6."""
+    h, r1, r2 = 0.9, 0.5, 0.6
+    inp = agents([(-50, 0, 0, 10, 0, -1, 40, 0, 0),      # soma 0; element 2 starts at (-10, 0, 0)
+                  (0, -50, h, 10, 0, -1, 0, 44, 0),      # soma 1; element 3 starts at (0, -6, h)
+                  (10, 0, 0, 2 * r1, 20, 0, 40, 0, 0),   # element along x, crossing at s = 0.5
+                  (0, 6, h, 2 * r2, 12, 1, 0, 44, 0)])   # element along y, crossing at s = 0.5
+    r = step(inp)
+    F = contact_F(r1 + r2 - h, r1, r2)
+    assert np.allclose(r["force"][2], [0, 0, -0.5 * F], atol=1e-12)
+    assert np.allclose(r["force"][0], [0, 0, -0.5 * F], atol=1e-12)
+    assert np.allclose(r["force"][3], [0, 0, 0.5 * F], atol=1e-12)
+    assert np.allclose(r["force"][1], [0, 0, 0.5 * F], atol=1e-12)
+
+
+def test_siblings_and_daughters_do_not_touch():
+    """Two daughters of one element overlap each other and their mother at the branch point."""
+    inp = agents([(0, 0, 0, 10, 0, -1, 0, 0, 0),
+                  (7, 0, 0, 1.0, 2.0, 0, 5, 0, 0),
+                  (8.5, 1, 0, 1.0, math.hypot(1.5, 1), 1, 0, 0, 0),
+                  (8.5, -1, 0, 1.0, math.hypot(1.5, 1), 1, 0, 0, 0)])
+    r = step(inp)
+    assert np.allclose(r["force"], 0.0, atol=1e-12)
+
+
+def test_somata_alone_reduce_to_sphere_mechanics():
+    n = 3000
+    x, y, z, d = synth.uniform_spheres(n, 120.0, seed=31)
+    inp = agents(np.stack([x, y, z, d.astype(np.float64), np.zeros(n), -np.ones(n),
+                           np.zeros(n), np.zeros(n), np.zeros(n)], 1))
+    r = step(inp)
+    m = oracle.mech_step(x, y, z, d, DT, K, GAM, CAP, want_force=True)
+    assert np.array_equal(r["neighbour_count"], m["neighbour_count"])
+    assert np.allclose(r["force"], m["force"], rtol=0, atol=1e-11)
+    for a in "xyz":
+        assert np.allclose(r[a], m[a], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed,side", [(1, 60.0), (2, 40.0), (3, 90.0)])
+def test_forest_conserves_force_and_counts_neighbours(seed, side):
+    params, inp = synth.neuron_forest(16, 2500, side=side, seed=seed)
+    r = step(inp)
+    f = r["force"]
+    assert np.abs(f.sum(0)).max() < 1e-11 * max(1.0, np.abs(f).sum())
+    assert np.abs(f).sum() > 1.0  # there are contacts and springs
+    # neighbours (R20) via a k-d tree over the binning points
+    m = inp["mother"].astype(np.int64)
+    el = m >= 0
+    b = np.stack([inp["x"], inp["y"], inp["z"]], 1)
+    q = b.copy()
+    q[el] = b[m[el]] + np.stack([inp["ox"], inp["oy"], inp["oz"]], 1)[el]
+    ln = np.linalg.norm(b - q, axis=1)
+    L = float(np.max(inp["diameter"] + ln))
+    assert r["L"] == pytest.approx(L, rel=1e-15)
+    mid = np.where(el[:, None], 0.5 * (q + b), b)
+    tree = cKDTree(mid)
+    cnt = np.array([len(v) - 1 for v in tree.query_ball_point(mid, L * (1 - 1e-12))])
+    assert np.array_equal(r["neighbour_count"], cnt)
+
+
+def test_forest_rotation_invariance():
+    params, inp = synth.neuron_forest(12, 1500, side=50.0, seed=4)
+    R = Rotation.from_rotvec([0.3, -1.1, 0.7]).as_matrix()
+    rot = dict(inp)
+    P = R @ np.stack([inp["x"], inp["y"], inp["z"]])
+    O = R @ np.stack([inp["ox"], inp["oy"], inp["oz"]])
+    for i, a in enumerate("xyz"):
+        rot[a] = np.ascontiguousarray(P[i])
+        rot["o" + a] = np.ascontiguousarray(O[i])
+    f0 = step(inp)["force"]
+    f1 = step(rot)["force"]
+    assert np.allclose(f1, (R @ f0.T).T, rtol=0, atol=1e-9 * np.abs(f0).max())
+
+
+def test_displacement_cap():
+    inp = agents([(0, 0, 0, 10, 0, -1, 0, 0, 0), (0.5, 0, 0, 10, 0, -1, 0, 0, 0)])
+    r = step(inp, dt=10.0, max_displacement=0.25)
+    assert r["x"][0] == pytest.approx(-0.25, abs=1e-15) and r["x"][1] == pytest.approx(0.75, abs=1e-15)
+
+
+def test_invalid_topology_is_rejected():
+    inp = agents([(0, 0, 0, 10, 0, 1, 0, 0, 0), (1, 0, 0, 1, 1, -1, 0, 0, 0)])  # mother after child
+    with pytest.raises(ValueError):
+        step(inp)
