@@ -331,7 +331,9 @@ def run_ours(args):
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
 
     sim.close()
-    ensemble = serving = plain = spheroid = stationary = oncology = None
+    ensemble = serving = plain = spheroid = stationary = oncology = neurite = None
+    if rank == 0 and args.neurite_agents > 0:
+        neurite = bench_neurite(args.neurite_agents)
     if rank == 0 and not args.no_small:
         plain = bench_plain()
         spheroid = bench_spheroid()
@@ -374,7 +376,7 @@ def run_ours(args):
             "diffusion": diffusion,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plain": plain, "spheroid": spheroid, "oncology": oncology, "stationary": stationary,
-            "ensemble": ensemble,
+            "neurite": neurite, "ensemble": ensemble,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -500,6 +502,66 @@ def bench_oncology(steps=100, p_apoptosis=0.02, sigma=0.5):
                         "migration sigma = %g um, growth, division and secretion into a 128^3 grid"
                         % (p_apoptosis, sigma),
             "steps": steps, "agents_start": n0, "agents_end": n1, "ms_per_step": ms / steps}
+
+
+NEURITE_BYTES_PER_AGENT = 92  # state read once (position 24, diameter 8, rest 8, mother 4,
+                              # offset 24) + position written (24)
+NEURITE_FORCE_BYTES_PER_AGENT = 92  # own record (40) + spring and bound (16) + key (4) read,
+                                    # output record (32) written
+
+
+def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_steps=2):
+    """Neurite mechanics on the neuron forest (somata with apical and basal dendrite trees, the
+    large pyramidal-cell run's 5000 cells and 9e6 agents), mixed precision: `steps` steps after
+    `warmup`, timed on the device; per-kernel times from a separately profiled step; the FP64 check
+    path timed over `fp64_steps` steps for comparison."""
+    from paper_2006_06775_gb300 import bdm
+    # other sizes keep the density and the cells' size: neurons and cube side scale with n
+    scale = n_agents / 9_000_000
+    neurons = max(1, int(round(neurons * scale)))
+    side = 2000.0 * scale ** (1.0 / 3.0)
+    params, inp = synth.neuron_forest(neurons, n_agents, side=side)
+    n = len(inp["x"])
+    out = {"workload": "neuron forest: %d somata (10 um) with 1 apical + 3 basal dendrite trees, "
+                       "%d agents, %.0f um cube, branching 0.038 / 0.006 per generation"
+                       % (neurons, n, side),
+           "agents": n, "steps": steps, "warmup": warmup, "precision": "mixed"}
+    params = dict(params, capacity=n, box_capacity=4 * n + 4096)
+    sim = bdm.Neurite(dict(params, precision="mixed"))
+    sim.set_agents(inp)
+    sim.step(warmup)
+    ms = _event_time_ms(sim.stream, lambda: sim.step(steps))
+    st = sim.get_state()
+    sim.profile(True)
+    sim.step(2)
+    kt = sim.kernel_times()
+    sim.profile(False)
+    sim.close()
+    per = {k: v[1] / v[0] for k, v in kt.items()}
+    peak, peak_kind = load_peaks()
+    fms = per.get("nr_force", float("nan"))
+    achieved = NEURITE_FORCE_BYTES_PER_AGENT * n / (fms * 1e-3) / 1e9
+    step_achieved = NEURITE_BYTES_PER_AGENT * n / (ms / steps * 1e-3) / 1e9
+    out.update({"ms_per_step": ms / steps, "agent_steps_per_s": n * steps / (ms * 1e-3),
+                "neighbours_per_agent": float(np.mean(st["neighbour_count"])),
+                "L_um": st["L"],
+                "kernels_ms_per_launch": {k: round(v, 4) for k, v in per.items()},
+                "roofline": {"bound": "hbm", "kernel": "nr_force", "achieved": achieved,
+                             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": peak_kind,
+                             "alg_bytes_per_agent": NEURITE_FORCE_BYTES_PER_AGENT,
+                             "traffic": None},
+                "step_roofline": {"bytes_per_agent_step": NEURITE_BYTES_PER_AGENT,
+                                  "achieved": step_achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": step_achieved / peak}})
+    if fp64_steps > 0:
+        sim = bdm.Neurite(dict(params, precision="fp64"))
+        sim.set_agents(inp)
+        sim.step(1)
+        ms64 = _event_time_ms(sim.stream, lambda: sim.step(fp64_steps))
+        sim.close()
+        out["fp64_ms_per_step"] = ms64 / fp64_steps
+    return out
 
 
 def bench_stationary(n=10_000_000, steps=10, warmup=3, skin=2.5):
@@ -661,11 +723,19 @@ def main():
     ap.add_argument("--ensemble-steps", type=int, default=1000)
     ap.add_argument("--ensemble-baseline-runs", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--neurite-agents", type=int, default=9_000_000,
+                    help="agents of the neuron-forest sub-benchmark (0: skip it)")
+    ap.add_argument("--neurite-only", action="store_true",
+                    help="run only the neuron-forest sub-benchmark and print its object")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.neurite_only:
+        print(json.dumps({"neurite": bench_neurite(args.neurite_agents, steps=args.steps,
+                                                   warmup=args.warmup)}), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -84,6 +84,11 @@ def lib():
                                        _f64p, _f64p, _f64p, ctypes.POINTER(NeuriteParams), _f64p,
                                        _f64p, _f64p, _u32p, ctypes.POINTER(ctypes.c_double),
                                        _f64p, _f64p, _f64p]
+        L.orc_neurite_sample.argtypes = [ctypes.c_size_t, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                         _i32p, _f64p, _f64p, _f64p,
+                                         ctypes.POINTER(NeuriteParams), ctypes.c_size_t, _i64p,
+                                         _f64p, _f64p, _f64p, _u32p,
+                                         ctypes.POINTER(ctypes.c_double)]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -186,6 +191,26 @@ def neurite_step(x, y, z, diam, rest, mother, ox, oy, oz, dt, repulsion, attract
         raise ValueError("orc_neurite_step rejected the input (%d)" % rc)
     return {"x": out["x"], "y": out["y"], "z": out["z"], "neighbour_count": nbr, "L": L.value,
             "force": np.stack([out["fx"], out["fy"], out["fz"]], axis=1)}
+
+
+def neurite_sample(x, y, z, diam, rest, mother, ox, oy, oz, dt, repulsion, attraction,
+                   max_displacement, spring, idx, interaction_radius=0.0):
+    """neurite_step's result for the agents idx only: dict of x, y, z, neighbour counts (sample
+    order) and L."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    m = len(idx)
+    p = NeuriteParams(dt, repulsion, attraction, max_displacement, spring, interaction_radius)
+    out = {k: np.zeros(m) for k in ("x", "y", "z")}
+    nbr = np.zeros(m, np.uint32)
+    L = ctypes.c_double(0.0)
+    rc = lib().orc_neurite_sample(len(x), _f64(x), _f64(y), _f64(z), _f64(diam), _f64(rest),
+                                  np.ascontiguousarray(mother, dtype=np.int32), _f64(ox),
+                                  _f64(oy), _f64(oz), ctypes.byref(p), m, idx, out["x"],
+                                  out["y"], out["z"], nbr, ctypes.byref(L))
+    if rc:
+        raise ValueError("orc_neurite_sample rejected the input (%d)" % rc)
+    out.update(neighbour_count=nbr, L=L.value)
+    return out
 
 
 def grow_divide(x, y, z, diam, vol, growth_volume, division_volume, offset_frac, seed, run, step):

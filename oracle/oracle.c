@@ -629,23 +629,87 @@ static void neurite_body(size_t a, const double* x, const double* y, const doubl
   }
 }
 
-int orc_neurite_step(size_t n, const double* x, const double* y, const double* z,
-                     const double* diam, const double* rest, const int32_t* mother,
-                     const double* ox, const double* oy, const double* oz,
-                     const orc_neurite_params* p, double* nx, double* ny, double* nz,
-                     uint32_t* nbr, double* L_out, double* fx, double* fy, double* fz) {
-  if (n == 0) return 0;
+/* Own and passed-up shares of the force on agent i and its neighbour count (R17-R20), over every
+ * other agent j in ascending id. */
+static void neurite_shares(size_t n, size_t i, const orc_body_t* B, const double* bin,
+                           const double* rest, const orc_neurite_params* p, double L2,
+                           double keep[3], double pass[3], uint32_t* cnt_out) {
+  const orc_body_t* bi = &B[i];
+  const double k = p->k_rep, gam = p->gamma_att;
+  uint32_t cnt = 0;
+  for (int c = 0; c < 3; ++c) { keep[c] = 0.0; pass[c] = 0.0; }
+  if (bi->mother >= 0 && bi->len > 0.0) {  /* R17 */
+    double T = p->k_spring * (bi->len - rest[i]) / rest[i];
+    for (int c = 0; c < 3; ++c) {
+      double f = T * (bi->ax[c] / bi->len);
+      keep[c] -= f;
+      pass[c] += f;
+    }
+  }
+  for (size_t j = 0; j < n; ++j) {
+    if (j == i) continue;
+    const orc_body_t* bj = &B[j];
+    double db[3] = {bin[3 * i] - bin[3 * j], bin[3 * i + 1] - bin[3 * j + 1],
+                    bin[3 * i + 2] - bin[3 * j + 2]};
+    double d2 = db[0] * db[0] + db[1] * db[1];
+    d2 = d2 + db[2] * db[2];
+    if (d2 < L2) cnt++;
+    /* R19 */
+    if (bi->mother == (int64_t)j || bj->mother == (int64_t)i) continue;
+    if (bi->mother >= 0 && bi->mother == bj->mother) continue;
+    double s = 0.0, t = 0.0;
+    orc_segment_closest(bi->q, bi->ax, bj->q, bj->ax, &s, &t);
+    double dv[3];
+    for (int c = 0; c < 3; ++c) dv[c] = (bi->q[c] + s * bi->ax[c]) - (bj->q[c] + t * bj->ax[c]);
+    double d = sqrt(dot3(dv, dv));
+    double delta = (bi->r + bj->r) - d;
+    if (delta > 0.0 && d > 0.0) {
+      double rho = (bi->r * bj->r) / (bi->r + bj->r);
+      double F = k * delta - gam * sqrt(rho * delta);
+      for (int c = 0; c < 3; ++c) {
+        double f = (F / d) * dv[c];
+        if (bi->mother < 0) {
+          keep[c] += f;
+        } else {
+          keep[c] += s * f;
+          pass[c] += (1.0 - s) * f;
+        }
+      }
+    }
+  }
+  *cnt_out = cnt;
+}
+
+/* R4 update of one agent from its summed force. */
+static void neurite_update(double x, double y, double z, const double S[3],
+                           const orc_neurite_params* p, double* nx, double* ny, double* nz) {
+  double Dx = p->dt * S[0], Dy = p->dt * S[1], Dz = p->dt * S[2];
+  double norm = Dx * Dx + Dy * Dy;
+  norm = sqrt(norm + Dz * Dz);
+  if (norm > p->max_disp) {
+    double f = p->max_disp / norm;
+    Dx = Dx * f; Dy = Dy * f; Dz = Dz * f;
+  }
+  *nx = x + Dx;
+  *ny = y + Dy;
+  *nz = z + Dz;
+}
+
+/* Validates the agents, builds every body and binning point and the radius L. */
+static int neurite_setup(size_t n, const double* x, const double* y, const double* z,
+                         const double* diam, const double* rest, const int32_t* mother,
+                         const double* ox, const double* oy, const double* oz,
+                         const orc_neurite_params* p, orc_body_t** B_out, double** bin_out,
+                         double* L_out) {
   for (size_t a = 0; a < n; ++a) {
     if (mother[a] >= (int64_t)a || mother[a] < -1) return -1;
     if (!(diam[a] > 0.0)) return -1;
     if (mother[a] >= 0 && !(rest[a] > 0.0)) return -1;
   }
-  orc_body_t* B = (orc_body_t*)malloc(n * sizeof(orc_body_t));
-  double* bin = (double*)malloc(3 * n * sizeof(double));
-  double* up = (double*)calloc(3 * n, sizeof(double));   /* what each element passes to its mother */
-  double* own = (double*)calloc(3 * n, sizeof(double));  /* what each agent keeps                  */
-  if (!B || !bin || !up || !own) {
-    free(B); free(bin); free(up); free(own);
+  orc_body_t* B = (orc_body_t*)malloc((n ? n : 1) * sizeof(orc_body_t));
+  double* bin = (double*)malloc((n ? 3 * n : 1) * sizeof(double));
+  if (!B || !bin) {
+    free(B); free(bin);
     return -2;
   }
   double L = p->interaction_radius;
@@ -656,57 +720,36 @@ int orc_neurite_step(size_t n, const double* x, const double* y, const double* z
     for (int k = 0; k < 3; ++k)
       bin[3 * a + k] = mother[a] < 0 ? B[a].p[k] : 0.5 * (B[a].q[k] + B[a].p[k]);
   }
+  *B_out = B;
+  *bin_out = bin;
+  *L_out = L;
+  return 0;
+}
+
+int orc_neurite_step(size_t n, const double* x, const double* y, const double* z,
+                     const double* diam, const double* rest, const int32_t* mother,
+                     const double* ox, const double* oy, const double* oz,
+                     const orc_neurite_params* p, double* nx, double* ny, double* nz,
+                     uint32_t* nbr, double* L_out, double* fx, double* fy, double* fz) {
+  if (n == 0) return 0;
+  orc_body_t* B = NULL;
+  double* bin = NULL;
+  double L = 0.0;
+  int rc = neurite_setup(n, x, y, z, diam, rest, mother, ox, oy, oz, p, &B, &bin, &L);
+  if (rc) return rc;
+  double* up = (double*)calloc(3 * n, sizeof(double));   /* what each element passes to its mother */
+  double* own = (double*)calloc(3 * n, sizeof(double));  /* what each agent keeps                  */
+  if (!up || !own) {
+    free(B); free(bin); free(up); free(own);
+    return -2;
+  }
   const double L2 = L * L;
-  const double k = p->k_rep, gam = p->gamma_att;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 256)
 #endif
   for (long long ii = 0; ii < (long long)n; ++ii) {
     size_t i = (size_t)ii;
-    const orc_body_t* bi = &B[i];
-    double keep[3] = {0.0, 0.0, 0.0}, pass[3] = {0.0, 0.0, 0.0};
-    uint32_t cnt = 0;
-    if (bi->mother >= 0 && bi->len > 0.0) {  /* R17 */
-      double T = p->k_spring * (bi->len - rest[i]) / rest[i];
-      for (int c = 0; c < 3; ++c) {
-        double f = T * (bi->ax[c] / bi->len);
-        keep[c] -= f;
-        pass[c] += f;
-      }
-    }
-    for (size_t j = 0; j < n; ++j) {
-      if (j == i) continue;
-      const orc_body_t* bj = &B[j];
-      double db[3] = {bin[3 * i] - bin[3 * j], bin[3 * i + 1] - bin[3 * j + 1],
-                      bin[3 * i + 2] - bin[3 * j + 2]};
-      double d2 = db[0] * db[0] + db[1] * db[1];
-      d2 = d2 + db[2] * db[2];
-      if (d2 < L2) cnt++;
-      /* R19 */
-      if (bi->mother == (int64_t)j || bj->mother == (int64_t)i) continue;
-      if (bi->mother >= 0 && bi->mother == bj->mother) continue;
-      double s = 0.0, t = 0.0;
-      orc_segment_closest(bi->q, bi->ax, bj->q, bj->ax, &s, &t);
-      double dv[3];
-      for (int c = 0; c < 3; ++c) dv[c] = (bi->q[c] + s * bi->ax[c]) - (bj->q[c] + t * bj->ax[c]);
-      double d = sqrt(dot3(dv, dv));
-      double delta = (bi->r + bj->r) - d;
-      if (delta > 0.0 && d > 0.0) {
-        double rho = (bi->r * bj->r) / (bi->r + bj->r);
-        double F = k * delta - gam * sqrt(rho * delta);
-        for (int c = 0; c < 3; ++c) {
-          double f = (F / d) * dv[c];
-          if (bi->mother < 0) {
-            keep[c] += f;
-          } else {
-            keep[c] += s * f;
-            pass[c] += (1.0 - s) * f;
-          }
-        }
-      }
-    }
-    for (int c = 0; c < 3; ++c) { own[3 * i + c] = keep[c]; up[3 * i + c] = pass[c]; }
-    nbr[i] = cnt;
+    neurite_shares(n, i, B, bin, rest, p, L2, &own[3 * i], &up[3 * i], &nbr[i]);
   }
   /* daughters pass their share to the mother, taken in ascending daughter id */
   for (size_t a = 0; a < n; ++a) {
@@ -715,20 +758,48 @@ int orc_neurite_step(size_t n, const double* x, const double* y, const double* z
     for (int c = 0; c < 3; ++c) own[3 * m + c] += up[3 * a + c];
   }
   for (size_t a = 0; a < n; ++a) {
-    double S[3] = {own[3 * a], own[3 * a + 1], own[3 * a + 2]};
+    const double* S = &own[3 * a];
     if (fx) { fx[a] = S[0]; fy[a] = S[1]; fz[a] = S[2]; }
-    double Dx = p->dt * S[0], Dy = p->dt * S[1], Dz = p->dt * S[2];
-    double norm = Dx * Dx + Dy * Dy;
-    norm = sqrt(norm + Dz * Dz);
-    if (norm > p->max_disp) {
-      double f = p->max_disp / norm;
-      Dx = Dx * f; Dy = Dy * f; Dz = Dz * f;
-    }
-    nx[a] = x[a] + Dx;
-    ny[a] = y[a] + Dy;
-    nz[a] = z[a] + Dz;
+    neurite_update(x[a], y[a], z[a], S, p, &nx[a], &ny[a], &nz[a]);
   }
   if (L_out) *L_out = L;
   free(B); free(bin); free(up); free(own);
+  return 0;
+}
+
+/* The same step for the m agents listed in idx only (their daughters' shares included): new
+ * positions and neighbour counts of those agents, O(m N).  For checks at sizes where the full
+ * O(N^2) step is out of reach. */
+int orc_neurite_sample(size_t n, const double* x, const double* y, const double* z,
+                       const double* diam, const double* rest, const int32_t* mother,
+                       const double* ox, const double* oy, const double* oz,
+                       const orc_neurite_params* p, size_t m, const int64_t* idx, double* nx,
+                       double* ny, double* nz, uint32_t* nbr, double* L_out) {
+  orc_body_t* B = NULL;
+  double* bin = NULL;
+  double L = 0.0;
+  for (size_t k = 0; k < m; ++k)
+    if (idx[k] < 0 || (size_t)idx[k] >= n) return -1;
+  int rc = neurite_setup(n, x, y, z, diam, rest, mother, ox, oy, oz, p, &B, &bin, &L);
+  if (rc) return rc;
+  const double L2 = L * L;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (long long kk = 0; kk < (long long)m; ++kk) {
+    size_t a = (size_t)idx[kk];
+    double S[3], pass[3], kd[3], pd[3];
+    uint32_t cnt = 0, cd = 0;
+    neurite_shares(n, a, B, bin, rest, p, L2, S, pass, &cnt);
+    for (size_t c = a + 1; c < n; ++c) {  /* daughters have larger ids */
+      if (mother[c] != (int32_t)a) continue;
+      neurite_shares(n, c, B, bin, rest, p, L2, kd, pd, &cd);
+      for (int q = 0; q < 3; ++q) S[q] += pd[q];
+    }
+    neurite_update(x[a], y[a], z[a], S, p, &nx[kk], &ny[kk], &nz[kk]);
+    nbr[kk] = cnt;
+  }
+  if (L_out) *L_out = L;
+  free(B); free(bin);
   return 0;
 }

@@ -106,6 +106,12 @@ int orc_neurite_step(size_t n, const double* x, const double* y, const double* z
                      const double* ox, const double* oy, const double* oz,
                      const orc_neurite_params* p, double* nx, double* ny, double* nz,
                      uint32_t* nbr, double* L_out, double* fx, double* fy, double* fz);
+/* The same step for the m agents idx[0..m-1] only (new positions and counts in sample order). */
+int orc_neurite_sample(size_t n, const double* x, const double* y, const double* z,
+                       const double* diam, const double* rest, const int32_t* mother,
+                       const double* ox, const double* oy, const double* oz,
+                       const orc_neurite_params* p, size_t m, const int64_t* idx, double* nx,
+                       double* ny, double* nz, uint32_t* nbr, double* L_out);
 
 /* Threads the OpenMP build uses (1 without OpenMP). */
 int orc_num_threads(void);

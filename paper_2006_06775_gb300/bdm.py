@@ -75,6 +75,16 @@ class BatchOptions(ctypes.Structure):
                 ("reserved0", ctypes.c_uint32)]
 
 
+class NeuriteParams(ctypes.Structure):
+    """Mirror of bdm_neurite_params (include/bdm_neurite.h)."""
+    _fields_ = [("struct_size", ctypes.c_uint32), ("precision", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("repulsion", ctypes.c_double),
+                ("attraction", ctypes.c_double), ("max_displacement", ctypes.c_double),
+                ("spring", ctypes.c_double), ("interaction_radius", ctypes.c_double),
+                ("capacity", ctypes.c_uint64), ("box_capacity", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -120,6 +130,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.bdm_batch_destroy.restype = None
     L.bdm_batch_last_error.argtypes = [vp]
     L.bdm_batch_last_error.restype = ctypes.c_char_p
+    L.bdm_neurite_create.argtypes = [ctypes.POINTER(NeuriteParams), ctypes.POINTER(vp)]
+    L.bdm_neurite_set_agents.argtypes = [vp, sz] + [vp] * 9
+    L.bdm_neurite_step.argtypes = [vp, i32]
+    L.bdm_neurite_get_state.argtypes = [vp, ctypes.POINTER(sz), vp, vp, vp, vp,
+                                        ctypes.POINTER(ctypes.c_double)]
+    L.bdm_neurite_profile.argtypes = [vp, i32]
+    L.bdm_neurite_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime), i32,
+                                           ctypes.POINTER(i32)]
+    L.bdm_neurite_destroy.argtypes = [vp]
+    L.bdm_neurite_destroy.restype = None
+    L.bdm_neurite_last_error.argtypes = [vp]
+    L.bdm_neurite_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -501,6 +523,96 @@ class Sim:
         if self.h:
             bdm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------------------
+# Neurite mechanics (include/bdm_neurite.h)
+# ------------------------------------------------------------------------------------------------
+NEURITE_FIELDS = ("x", "y", "z", "diameter", "rest", "mother", "ox", "oy", "oz")
+
+
+class Neurite:
+    """One neurite-mechanics handle (somata and neurite elements).  params: dict as produced by
+    ``synth.neuron_forest`` plus ``precision`` ("mixed" or "fp64") and ``capacity``."""
+
+    def __init__(self, params: dict, stream=None):
+        import torch
+        self.params = dict(params)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        p = NeuriteParams()
+        p.struct_size = ctypes.sizeof(NeuriteParams)
+        p.precision = BDM_MIXED if self.params.get("precision", "mixed") == "mixed" else BDM_FP64
+        for k in ("dt", "repulsion", "attraction", "max_displacement", "spring",
+                  "interaction_radius"):
+            setattr(p, k, float(self.params.get(k, 0.0)))
+        p.capacity = int(self.params.get("capacity", 1 << 20))
+        p.box_capacity = int(self.params.get("box_capacity", 0))
+        p.stream = self.stream.cuda_stream
+        L = load()
+        h = ctypes.c_void_p()
+        rc = L.bdm_neurite_create(ctypes.byref(p), ctypes.byref(h))
+        if rc != BDM_OK:
+            msg = L.bdm_neurite_last_error(h).decode() if h.value else ""
+            L.bdm_neurite_destroy(h)
+            raise BdmError(rc, msg)
+        self.h = h
+        self._keep = None
+
+    def _check(self, rc):
+        if rc != BDM_OK:
+            raise BdmError(rc, load().bdm_neurite_last_error(self.h).decode())
+
+    def set_agents(self, inp: dict):
+        """inp: x, y, z, diameter, rest, ox, oy, oz (float64) and mother (int32), one entry per
+        agent in id order."""
+        arrs = [np.ascontiguousarray(inp[k], np.int32 if k == "mother" else np.float64)
+                for k in NEURITE_FIELDS]
+        n = len(arrs[0])
+        if any(len(a) != n for a in arrs):
+            raise ValueError("neurite input arrays differ in length")
+        self._keep = arrs  # alive until the copies are done (the call synchronises)
+        self._check(load().bdm_neurite_set_agents(self.h, n, *[_ptr(a) for a in arrs]))
+        self._keep = None
+
+    def step(self, n: int = 1):
+        self._check(load().bdm_neurite_step(self.h, int(n)))
+
+    def get_state(self) -> dict:
+        L = load()
+        n = ctypes.c_size_t(0)
+        self._check(L.bdm_neurite_get_state(self.h, ctypes.byref(n), None, None, None, None,
+                                            None))
+        n = n.value
+        out = {k: np.zeros(n) for k in ("x", "y", "z")}
+        nbr = np.zeros(n, np.uint32)
+        Lr = ctypes.c_double(0.0)
+        m = ctypes.c_size_t(0)
+        self._check(L.bdm_neurite_get_state(self.h, ctypes.byref(m), _ptr(out["x"]),
+                                            _ptr(out["y"]), _ptr(out["z"]), _ptr(nbr),
+                                            ctypes.byref(Lr)))
+        out.update(n=n, neighbour_count=nbr, L=Lr.value)
+        return out
+
+    def profile(self, enable=True):
+        self._check(load().bdm_neurite_profile(self.h, 1 if enable else 0))
+
+    def kernel_times(self):
+        arr = (KernelTime * 64)()
+        cnt = ctypes.c_int(0)
+        self._check(load().bdm_neurite_kernel_times(self.h, arr, 64, ctypes.byref(cnt)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+                for i in range(min(cnt.value, 64))}
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().bdm_neurite_destroy(self.h)
+        self.h = None
 
     def __del__(self):
         try:

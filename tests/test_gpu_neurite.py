@@ -1,0 +1,157 @@
+"""GPU parity of neurite mechanics (readings R16-R20) through the C ABI of include/bdm_neurite.h.
+
+Every step is checked against the FP64 oracle from the GPU's own state (teacher forcing): the
+neighbour counts and the radius L exactly, positions within 1e-9 um on the FP64 path and 1e-5 um on
+the mixed path (FP32 contact geometry from box-relative offsets; an FP32 force of magnitude F carries
+about 1e-6 F of error, moved by dt = 0.01).  At the benchmark's full size (5000 neurons, 9e6
+agents) sampled agents are checked against the oracle one by one."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_06775_gb300 import bdm, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "mixed": 1e-5}
+
+
+def oracle_step(params, inp):
+    return oracle.neurite_step(inp["x"], inp["y"], inp["z"], inp["diameter"], inp["rest"],
+                               inp["mother"], inp["ox"], inp["oy"], inp["oz"], params["dt"],
+                               params["repulsion"], params["attraction"],
+                               params["max_displacement"], params["spring"],
+                               params.get("interaction_radius", 0.0))
+
+
+def make(params, precision, capacity=None, **kw):
+    p = dict(params, precision=precision, capacity=capacity or (1 << 16), **kw)
+    return bdm.Neurite(p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("seed,neurons,agents,side", [(1, 16, 2500, 60.0), (2, 40, 9001, 70.0),
+                                                      (3, 3, 700, 25.0)])
+def test_forest_teacher_forced(precision, seed, neurons, agents, side):
+    params, inp = synth.neuron_forest(neurons, agents, side=side, seed=seed)
+    sim = make(params, precision)
+    sim.set_agents(inp)
+    cur = dict(inp)
+    contacts_seen = 0.0
+    for k in range(4):
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle_step(params, cur)
+        assert got["n"] == agents
+        assert got["L"] == want["L"], k
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        for a in "xyz":
+            err = np.max(np.abs(got[a] - want[a]))
+            assert err < TOL[precision], (k, a, err)
+        contacts_seen = max(contacts_seen, float(np.abs(want["force"]).max()))
+        cur = dict(cur, x=got["x"], y=got["y"], z=got["z"])
+    assert contacts_seen > 0.0
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_many_steps_stay_close_to_the_oracle(precision):
+    """20 free-running steps on both sides (no teacher forcing)."""
+    params, inp = synth.neuron_forest(10, 1500, side=40.0, seed=7)
+    sim = make(params, precision)
+    sim.set_agents(inp)
+    sim.step(20)
+    got = sim.get_state()
+    cur = dict(inp)
+    for _ in range(20):
+        r = oracle_step(params, cur)
+        cur = dict(cur, x=r["x"], y=r["y"], z=r["z"])
+    for a in "xyz":
+        assert np.max(np.abs(got[a] - cur[a])) < 20 * TOL[precision]
+    assert np.array_equal(got["neighbour_count"], r["neighbour_count"])
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_somata_only_and_single_agents(precision):
+    params, _ = synth.neuron_forest(1, 1, seed=0)
+    x, y, z, d = synth.uniform_spheres(3000, 100.0, seed=8)
+    n = len(x)
+    inp = dict(x=x, y=y, z=z, diameter=d.astype(np.float64), rest=np.zeros(n),
+               mother=-np.ones(n, np.int32), ox=np.zeros(n), oy=np.zeros(n), oz=np.zeros(n))
+    sim = make(params, precision)
+    sim.set_agents(inp)
+    sim.step(1)
+    got = sim.get_state()
+    want = oracle_step(params, inp)
+    assert np.array_equal(got["neighbour_count"], want["neighbour_count"])
+    for a in "xyz":
+        assert np.max(np.abs(got[a] - want[a])) < TOL[precision]
+    # one soma and one element: only the spring acts
+    one = {k: v[:1].copy() for k, v in inp.items()}
+    two = {k: np.concatenate([one[k], np.asarray([v], one[k].dtype)]) for k, v in
+           dict(x=x[0] + 7.5, y=y[0], z=z[0], diameter=1.0, rest=2.0, mother=0, ox=5.0, oy=0.0,
+                oz=0.0).items()}
+    for case in (one, two):
+        sim.set_agents(case)
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle_step(params, case)
+        for a in "xyz":
+            assert np.max(np.abs(got[a] - want[a])) < TOL[precision]
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"])
+    # no agents: steps are a no-op
+    sim.set_agents({k: v[:0] for k, v in inp.items()})
+    sim.step(3)
+    assert sim.get_state()["n"] == 0
+    sim.close()
+
+
+def test_errors_are_reported_without_a_fault():
+    params, inp = synth.neuron_forest(8, 800, side=40.0, seed=9)
+    sim = make(params, "mixed", box_capacity=8)
+    sim.set_agents(inp)
+    sim.step(1)
+    with pytest.raises(bdm.BdmError) as e:
+        sim.get_state()
+    assert e.value.code == bdm.BDM_ENOMEM
+    sim.close()
+    sim = make(params, "mixed", capacity=100)
+    with pytest.raises(bdm.BdmError) as e:
+        sim.set_agents(inp)
+    assert e.value.code == bdm.BDM_ENOMEM
+    sim.close()
+    sim = make(params, "fp64")
+    bad = dict(inp, mother=inp["mother"].copy())
+    bad["mother"][20] = 25
+    with pytest.raises(bdm.BdmError) as e:
+        sim.set_agents(bad)
+    assert e.value.code == bdm.BDM_EINVAL and "agent 20" in str(e.value)
+    sim.close()
+
+
+def test_full_size_forest_sampled_against_the_oracle():
+    """The benchmark workload (5000 neurons, 9e6 agents, mixed precision, the bench's launch
+    configuration): 48 sampled agents against the oracle one by one, exact neighbour counts; and
+    the total displacement of all agents is zero up to rounding when no cap is hit (every force
+    comes in equal and opposite pairs, and the split and the springs only move force around)."""
+    params, inp = synth.neuron_forest()
+    n = len(inp["x"])
+    sim = make(params, "mixed", capacity=n)
+    sim.set_agents(inp)
+    sim.step(1)
+    got = sim.get_state()
+    g = synth.rng(77)
+    idx = np.unique(np.concatenate([g.integers(0, n, 40), g.integers(0, 5000, 8)]))
+    want = oracle.neurite_sample(inp["x"], inp["y"], inp["z"], inp["diameter"], inp["rest"],
+                                 inp["mother"], inp["ox"], inp["oy"], inp["oz"], params["dt"],
+                                 params["repulsion"], params["attraction"],
+                                 params["max_displacement"], params["spring"], idx)
+    assert got["L"] == want["L"]
+    assert np.array_equal(got["neighbour_count"][idx], want["neighbour_count"])
+    for a in "xyz":
+        assert np.max(np.abs(got[a][idx] - want[a])) < TOL["mixed"]
+    d = np.stack([got[a] - inp[a] for a in "xyz"], 1)
+    assert np.abs(d).max() < params["max_displacement"]
+    assert np.abs(d.sum(0)).max() < 1e-6 * np.abs(d).sum()
+    sim.close()

@@ -192,3 +192,16 @@ def test_invalid_topology_is_rejected():
     inp = agents([(0, 0, 0, 10, 0, 1, 0, 0, 0), (1, 0, 0, 1, 1, -1, 0, 0, 0)])  # mother after child
     with pytest.raises(ValueError):
         step(inp)
+
+
+def test_sampled_step_equals_the_full_step():
+    params, inp = synth.neuron_forest(16, 2500, side=50.0, seed=5)
+    full = step(inp)
+    idx = np.array([0, 3, 15, 16, 17, 100, 777, 2499])
+    smp = oracle.neurite_sample(inp["x"], inp["y"], inp["z"], inp["diameter"], inp["rest"],
+                                inp["mother"], inp["ox"], inp["oy"], inp["oz"], DT, K, GAM, CAP,
+                                KS, idx)
+    assert np.array_equal(smp["neighbour_count"], full["neighbour_count"][idx])
+    for a in "xyz":
+        assert np.array_equal(smp[a], full[a][idx])
+    assert smp["L"] == full["L"]
