@@ -158,8 +158,9 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_prepare(
     double k_spring, double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
     float4* __restrict__ spr, Dbl4* __restrict__ spr64, float4* __restrict__ axr,
     double* __restrict__ partials) {
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  double ext = 0.0;
+  // bounds in the order-preserving integer encoding of doubles (integer compares; GB300's FP64
+  // pipe is narrow)
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull}, ext = 0ull;
   for (unsigned a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
     const double px = x[a], py = y[a], pz = z[a];
     const int m = mother[a];
@@ -202,19 +203,21 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_prepare(
     else spr64[a] = f64;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      mn[c] = fmin(mn[c], b[c]);
-      mx[c] = fmax(mx[c], b[c]);
+      const unsigned long long eb = enc_double(b[c]);
+      mn[c] = eb < mn[c] ? eb : mn[c];
+      mx[c] = eb > mx[c] ? eb : mx[c];
     }
-    ext = fmax(ext, e);
+    const unsigned long long ee = enc_double(e);
+    ext = ee > ext ? ee : ext;
   }
-  __shared__ double s_red[kNrBlock / 32][kNrPartialWords];
-  double v[kNrPartialWords] = {mn[0], mn[1], mn[2], mx[0], mx[1], mx[2], ext};
+  __shared__ unsigned long long s_red[kNrBlock / 32][kNrPartialWords];
+  unsigned long long v[kNrPartialWords] = {mn[0], mn[1], mn[2], mx[0], mx[1], mx[2], ext};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
     for (int k = 0; k < kNrPartialWords; ++k) {
-      const double w = __shfl_down_sync(0xffffffffu, v[k], o);
-      v[k] = k < 3 ? fmin(v[k], w) : fmax(v[k], w);
+      const unsigned long long w = __shfl_down_sync(0xffffffffu, v[k], o);
+      v[k] = k < 3 ? (w < v[k] ? w : v[k]) : (w > v[k] ? w : v[k]);
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -223,9 +226,14 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_prepare(
   __syncthreads();
   if (threadIdx.x < kNrPartialWords) {
     const int k = threadIdx.x;
-    double r = s_red[0][k];
-    for (int w = 1; w < kNrBlock / 32; ++w) r = k < 3 ? fmin(r, s_red[w][k]) : fmax(r, s_red[w][k]);
-    partials[blockIdx.x * kNrPartialWords + k] = r;
+    unsigned long long r = s_red[0][k];
+    for (int w = 1; w < kNrBlock / 32; ++w) {
+      const unsigned long long q = s_red[w][k];
+      r = k < 3 ? (q < r ? q : r) : (q > r ? q : r);
+    }
+    // empty blocks leave the identities: +inf / -inf / 0 once decoded
+    partials[blockIdx.x * kNrPartialWords + k] =
+        r == ~0ull ? INFINITY : (r == 0ull ? (k < 6 ? -INFINITY : 0.0) : dec_double(r));
   }
 }
 
@@ -327,13 +335,29 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_key(unsigned n, const double* _
   }
 }
 
+// mixed records of one box-ordered slot: A = (binning point - box corner, half extent bound) in a
+// dense array (the sweep reads only A), and one 32 B sector holding B = (axis p - q, radius) and the
+// (id, mother) pair, which only contacts and exclusions read
+struct alignas(32) NrRecB {
+  float4 B;
+  int2 C;
+  int2 pad;
+};
+
 struct NrRecords {
   Dbl4* A64;     // FP64: (q, r)
   Dbl4* B64;     // FP64: (p, half extent bound)
-  float4* A32;   // mixed: (binning point - box corner, half extent bound)
-  float4* B32;   // mixed: (axis p - q, r)
-  int2* C;       // (id, mother)
+  float4* A32;   // mixed: A records
+  NrRecB* RB;    // mixed: B + (id, mother) records
+  int2* C;       // FP64: (id, mother)
 };
+
+// (id, mother) of a box-ordered slot
+template <bool MIXED>
+__device__ __forceinline__ int2 rec_c(const NrRecords& rec, unsigned u) {
+  if constexpr (MIXED) return rec.RB[u].C;
+  else return rec.C[u];
+}
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kNrBlock) k_nr_scatter(
@@ -357,9 +381,12 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_scatter(
       const float o0 = (float)(bx[a] - (g->origin[0] + (double)ix * Lbox));
       const float o1 = (float)(by[a] - (g->origin[1] + (double)iy * Lbox));
       const float o2 = (float)(bz[a] - (g->origin[2] + (double)iz * Lbox));
-      rec.C[slot] = make_int2((int)a, m);
       rec.A32[slot] = make_float4(o0, o1, o2, spr[a].w);
-      rec.B32[slot] = axr[a];
+      NrRecB r;
+      r.B = axr[a];
+      r.C = make_int2((int)a, m);
+      r.pad = make_int2(0, 0);
+      rec.RB[slot] = r;
       continue;
     }
     const double p[3] = {x[a], y[a], z[a]};
@@ -405,7 +432,7 @@ __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
   const T k = (T)k_rep, gam = (T)gamma;
   __shared__ unsigned s_def[MIXED ? kNrList : 1][kNrForceBlock];
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int2 ci = rec.C[t];
+    const int2 ci = rec_c<MIXED>(rec, t);
     const int i = ci.x, mi = ci.y;
     const unsigned kb = key[i];
     const int ix = (int)(kb % (unsigned)d0), iy = (int)((kb / (unsigned)d0) % (unsigned)d1),
@@ -427,7 +454,7 @@ __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
     double bi[3];  // FP64 binning point (FP64 kernel: always; mixed: loaded when a test needs it)
     bool have_bi = false;
     if constexpr (MIXED) {
-      const float4 A = rec.A32[t], B = rec.B32[t];
+      const float4 A = rec.A32[t], B = rec.RB[t].B;
       ai[0] = B.x; ai[1] = B.y; ai[2] = B.z; ri = B.w;
       bfi[0] = A.x; bfi[1] = A.y; bfi[2] = A.z;
       // geometry relative to the box corner: q = b - a / 2
@@ -449,50 +476,68 @@ __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
       for (int dy = -1; dy <= 1; ++dy) {
         const int by2 = iy + dy;
         if (by2 < 0 || by2 >= d1) continue;
-        const unsigned row = (unsigned)d0 * ((unsigned)by2 + (unsigned)d1 * (unsigned)bz2);
-        // slots of boxes x0..x1 of this row are contiguous: [s[0], s[x1 - x0 + 1])
-        unsigned sb[4];
+        const unsigned row = (unsigned)d0 * ((unsigned)by2 + (unsigned)d1 * (unsigned)bz2) + (unsigned)x0;
+        // slots of boxes x0..x1 of this row are contiguous: box b of the run holds [s_b, s_b+1);
+        // missing boxes (at the grid's x faces) repeat the last bound, so the run ends at s3
         const int nb = x1 - x0 + 1;
-        for (int q = 0; q <= nb; ++q) sb[q] = start[row + (unsigned)(x0 + q)];
+        const unsigned s0 = start[row], s1 = start[row + 1];
+        const unsigned s2 = nb >= 2 ? start[row + 2] : s1;
+        const unsigned s3 = nb >= 3 ? start[row + 3] : s2;
         const float shy = (float)dy * Lf, shz = (float)dz * Lf;
         int bxc = 0;  // box of the run the slot u is in
-        for (unsigned u = sb[0]; u < sb[nb]; ++u) {
-          while (u >= sb[bxc + 1]) ++bxc;
-          if (u == t) continue;
-          const int dx = x0 + bxc - ix;
-          if constexpr (MIXED) {
+        unsigned nxt = s1;
+        if constexpr (MIXED) {
+          // i's binning point minus the candidate box's corner shift: e = ebase - A.xyz
+          float ex = bfi[0] - (float)(x0 - ix) * Lf;
+          const float ey = bfi[1] - shy, ez = bfi[2] - shz;
+          for (unsigned u = s0; u < s3; ++u) {
+            while (u >= nxt) {
+              ++bxc;
+              nxt = bxc == 1 ? s2 : s3;
+              ex = bfi[0] - (float)(x0 + bxc - ix) * Lf;
+            }
             const float4 A = rec.A32[u];
-            // binning point of j relative to i's box corner
-            const float rel[3] = {A.x + (float)dx * Lf, A.y + shy, A.z + shz};
-            const float e0 = bfi[0] - rel[0], e1 = bfi[1] - rel[1], e2 = bfi[2] - rel[2];
+            const float e0 = ex - A.x, e1 = ey - A.y, e2 = ez - A.z;
             const float d2f = (e0 * e0 + e1 * e1) + e2 * e2;
+            // beyond L (widened by the FP32 band) j is neither a neighbour nor, by R20, a contact
+            if (d2f >= L2hi) continue;
+            // i itself has d2f = 0 exactly: it is counted here and taken off after the sweep
             if (d2f < L2lo) {
               ++cnt;
-            } else if (d2f < L2hi) {
+            } else {
               if (!have_bi) {
                 bi[0] = bx[i]; bi[1] = by[i]; bi[2] = bz[i];
                 have_bi = true;
               }
-              const int j = rec.C[u].x;
+              const int j = rec_c<MIXED>(rec, u).x;
               const double e[3] = {__dsub_rn(bi[0], bx[j]), __dsub_rn(bi[1], by[j]),
                                    __dsub_rn(bi[2], bz[j])};
               if (dot3_rn(e[0], e[1], e[2], e[0], e[1], e[2]) < L2) ++cnt;
             }
             const float hs = (hi + A.w) * 1.0001f + 1e-4f;
-            if (d2f >= hs * hs) continue;
-            const int2 cj = rec.C[u];
+            if (d2f >= hs * hs || u == t) continue;
+            const int2 cj = rec_c<MIXED>(rec, u);
             if (mi == cj.x || cj.y == i || (mi >= 0 && mi == cj.y)) continue;
+            const int dx = x0 + bxc - ix;
             if (ndef < kNrList) {
               // deferred: evaluated with the warp's other contacts after the sweep
               s_def[ndef][threadIdx.x] = u | ((unsigned)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) << kNrSlotBits);
               ++ndef;
               continue;
             }
-            const float4 B = rec.B32[u];
+            const float4 B = rec.RB[u].B;
+            const float rel[3] = {A.x + (float)dx * Lf, A.y + shy, A.z + shz};
             const float aj[3] = {B.x, B.y, B.z};
             const float qj[3] = {rel[0] - 0.5f * B.x, rel[1] - 0.5f * B.y, rel[2] - 0.5f * B.z};
             contact<float>(qi, ai, ri, mi >= 0, qj, aj, B.w, k, gam, keep, pass);
-          } else {
+          }
+        } else {
+          for (unsigned u = s0; u < s3; ++u) {
+            while (u >= nxt) {
+              ++bxc;
+              nxt = bxc == 1 ? s2 : s3;
+            }
+            if (u == t) continue;
             const Dbl4 A = rec.A64[u], B = rec.B64[u];
             const double bj0 = __dmul_rn(0.5, __dadd_rn(A.x, B.x));
             const double bj1 = __dmul_rn(0.5, __dadd_rn(A.y, B.y));
@@ -513,13 +558,14 @@ __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
       }
     }
     if constexpr (MIXED) {
+      cnt -= 1u;  // i itself
       // second pass: the deferred contacts (the sweep above only counted and filtered, so lanes
       // run this with far less divergence than contacts evaluated inside the sweep)
       for (int e = 0; e < ndef; ++e) {
         const unsigned w = s_def[e][threadIdx.x];
         const unsigned u = w & ((1u << kNrSlotBits) - 1u), code = w >> kNrSlotBits;
         const int dx = (int)(code % 3u) - 1, dy = (int)((code / 3u) % 3u) - 1, dz = (int)(code / 9u) - 1;
-        const float4 A = rec.A32[u], B = rec.B32[u];
+        const float4 A = rec.A32[u], B = rec.RB[u].B;
         const float rel[3] = {A.x + (float)dx * Lf, A.y + (float)dy * Lf, A.z + (float)dz * Lf};
         const float aj[3] = {B.x, B.y, B.z};
         const float qj[3] = {rel[0] - 0.5f * B.x, rel[1] - 0.5f * B.y, rel[2] - 0.5f * B.z};
@@ -547,7 +593,29 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_update(
     unsigned* __restrict__ nbr, const NrGrid* g, double dt, double cap) {
   if (g->nbox == 0) return;
   const double cap2 = cap * cap;
+  const float dtf = (float)dt, capf = (float)cap, cap2f = capf * capf;
   for (unsigned a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+    if constexpr (MIXED) {
+      // FP32 sum and cap (the shares are FP32), exact conversion, one FP64 add per axis
+      const float4 kp = out32[a].keep;
+      float F0 = kp.x, F1 = kp.y, F2 = kp.z;
+      const unsigned c1 = cstart[a + 1];
+      for (unsigned c = cstart[a]; c < c1; ++c) {
+        const float4 ps = out32[clist[c]].pass;
+        F0 += ps.x; F1 += ps.y; F2 += ps.z;
+      }
+      float D0 = dtf * F0, D1 = dtf * F1, D2 = dtf * F2;
+      const float nn = (D0 * D0 + D1 * D1) + D2 * D2;
+      if (nn > cap2f) {
+        const float f = capf * rsqrtf(nn);
+        D0 *= f; D1 *= f; D2 *= f;
+      }
+      nx[a] = __dadd_rn(x[a], f2d_exact(D0));
+      ny[a] = __dadd_rn(y[a], f2d_exact(D1));
+      nz[a] = __dadd_rn(z[a], f2d_exact(D2));
+      nbr[a] = __float_as_uint(kp.w);
+      continue;
+    }
     double S0, S1, S2;
     unsigned cnt;
     if constexpr (MIXED) {
@@ -849,16 +917,18 @@ int bdm_neurite_create(const bdm_neurite_params* p, bdm_neurite** out) {
       (rc = nalloc(s, &s->spr, C)) ||
       (rc = nalloc(s, &s->key, C)) || (rc = nalloc(s, &s->rank, C)) || (rc = nalloc(s, &s->nbr, C)) ||
       (rc = nalloc(s, &s->cstart, C + 1)) || (rc = nalloc(s, &s->clist, C)) ||
-      (rc = nalloc(s, &s->rec.C, C)) || (rc = nalloc(s, &s->count, B + 1)) ||
+      (rc = nalloc(s, &s->count, B + 1)) ||
       (rc = nalloc(s, &s->start, B + 1)) || (rc = nalloc(s, &s->partials, kNrMaxPartials * kNrPartialWords)))
     return rc;
   s->max_tiles = (unsigned)((B + 1 + kScanTile - 1) / kScanTile) + 1u;
   if ((rc = nalloc(s, &s->tiles, s->max_tiles))) return rc;
   if (s->mixed) {
-    if ((rc = nalloc(s, &s->rec.A32, C)) || (rc = nalloc(s, &s->rec.B32, C))) return rc;
+    if ((rc = nalloc(s, &s->rec.A32, C)) || (rc = nalloc(s, &s->rec.RB, C))) return rc;
     if ((rc = nalloc(s, &s->out32, C)) || (rc = nalloc(s, &s->axr, C))) return rc;
   } else {
-    if ((rc = nalloc(s, &s->rec.A64, C)) || (rc = nalloc(s, &s->rec.B64, C))) return rc;
+    if ((rc = nalloc(s, &s->rec.A64, C)) || (rc = nalloc(s, &s->rec.B64, C)) ||
+        (rc = nalloc(s, &s->rec.C, C)))
+      return rc;
     if ((rc = nalloc(s, &s->out64, C)) || (rc = nalloc(s, &s->spr64, C))) return rc;
   }
   NCK(cudaMemsetAsync(s->count, 0, sizeof(unsigned) * (B + 1), s->stream));
