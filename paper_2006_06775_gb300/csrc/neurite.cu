@@ -490,13 +490,17 @@ __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
           // i's binning point minus the candidate box's corner shift: e = ebase - A.xyz
           float ex = bfi[0] - (float)(x0 - ix) * Lf;
           const float ey = bfi[1] - shy, ez = bfi[2] - shz;
+          // software-pipelined: the next candidate's record is requested before this one is
+          // tested, so each lane keeps two loads in flight
+          float4 An = s0 < s3 ? rec.A32[s0] : make_float4(0.f, 0.f, 0.f, 0.f);
           for (unsigned u = s0; u < s3; ++u) {
+            const float4 A = An;
+            if (u + 1 < s3) An = rec.A32[u + 1];
             while (u >= nxt) {
               ++bxc;
               nxt = bxc == 1 ? s2 : s3;
               ex = bfi[0] - (float)(x0 + bxc - ix) * Lf;
             }
-            const float4 A = rec.A32[u];
             const float e0 = ex - A.x, e1 = ey - A.y, e2 = ez - A.z;
             const float d2f = (e0 * e0 + e1 * e1) + e2 * e2;
             // beyond L (widened by the FP32 band) j is neither a neighbour nor, by R20, a contact
