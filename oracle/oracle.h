@@ -12,8 +12,11 @@
  *   - agent operations (behaviours, mechanical forces) vs standalone operations (diffusion):
  *     Section "Simulation concepts" (operations paragraph);
  *   - sphere-sphere force: the paper states only that it uses the Cortex3D method (Section
- *     "Performance"); the law below is the reading documented in the design doc (readings R1-R4);
- *   - SIR behaviours and counting operation: Section "Epidemiology use case".
+ *     "Performance"); the law used here (readings R1-R4) is stated beside orc_mech_step;
+ *   - SIR behaviours and counting operation: Section "Epidemiology use case";
+ *   - neurite elements (cylinders with a spring and a distal point mass, joined as trees): Section
+ *     "Neuroscience module"; their contact law (readings R16-R20) is stated beside
+ *     orc_neurite_step in oracle.c.
  *
  * Conventions: all arrays are caller-owned, in agent-id order unless stated; functions return 0 on
  * success and a negative code on invalid input (-1) or allocation failure (-2).

@@ -22,6 +22,9 @@ benchmark, Sec. "Oncology use case" the tumour spheroid, Sec. "Epidemiology use 
   settled_mechanics   a settled lattice (spacing 14 um, no contacts) around a central ball of
                       overlapping agents at 0.3 volume fraction (10% of the agents), seed 5: the
                       workload on which skipping stationary agents is measured.
+  neuron_forest       5000 somata (10 um) in a 2000 um cube with one apical and three basal
+                      dendrite trees each (branching 0.038 / 0.006 per generation, apical elements
+                      twice as long), 9e6 agents, seed 6: the large pyramidal-cell run's size.
 """
 import math
 from dataclasses import dataclass
