@@ -94,3 +94,40 @@ def test_sir_parameters_are_checked(lib):
     h = ctypes.c_void_p()
     assert lib.bdm_create(ctypes.byref(p), ctypes.byref(h)) == bdm.BDM_EINVAL
     lib.bdm_destroy(h)
+
+
+@pytest.mark.parametrize("change,fragment", [
+    ({"precision": 7}, b"precision"),
+    ({"dt": 0.0}, b"dt"),
+    ({"max_displacement": -1.0}, b"max_displacement"),
+    ({"capacity": 0}, b"capacity"),
+    ({"capacity": (1 << 27) + 1}, b"2^27"),
+    ({"interaction_radius": float("nan")}, b"interaction_radius"),
+])
+def test_neurite_parameters_are_rejected_before_any_cuda_call(lib, change, fragment):
+    p = bdm.NeuriteParams()
+    p.struct_size = ctypes.sizeof(bdm.NeuriteParams)
+    p.precision = bdm.BDM_MIXED
+    p.dt, p.repulsion, p.attraction, p.max_displacement, p.spring = 0.01, 2.0, 1.0, 3.0, 10.0
+    p.capacity = 1000
+    for k, v in change.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    rc = lib.bdm_neurite_create(ctypes.byref(p), ctypes.byref(h))
+    assert rc == bdm.BDM_EINVAL
+    assert fragment in lib.bdm_neurite_last_error(h)
+    lib.bdm_neurite_destroy(h)
+
+
+def test_neurite_struct_size_check(lib):
+    p = bdm.NeuriteParams()
+    p.struct_size = ctypes.sizeof(bdm.NeuriteParams) - 8
+    h = ctypes.c_void_p()
+    assert lib.bdm_neurite_create(ctypes.byref(p), ctypes.byref(h)) == bdm.BDM_EINVAL
+    assert not h.value
+    # valid parameters pass validation; without a GPU creation then fails with BDM_ECUDA
+    p.struct_size = ctypes.sizeof(bdm.NeuriteParams)
+    p.precision, p.dt, p.max_displacement, p.capacity = bdm.BDM_FP64, 0.01, 3.0, 100
+    rc = lib.bdm_neurite_create(ctypes.byref(p), ctypes.byref(h))
+    assert rc in (bdm.BDM_OK, bdm.BDM_ECUDA), lib.bdm_neurite_last_error(h)
+    lib.bdm_neurite_destroy(h)
