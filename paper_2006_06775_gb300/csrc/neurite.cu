@@ -8,17 +8,19 @@
 //
 // One step, all on the handle's stream (captured once per position parity into a CUDA graph):
 //   k_nr_prepare   id order: proximal point, binning point, extent and spring of every agent, and
-//                  per-block bounds / largest extent                       (reads 84 B, writes 40 B)
+//                  per-block bounds / largest extent    (reads 84 B, writes 56 B mixed / 72 B FP64)
 //   k_nr_finalize  one block: origin, L, box length, boxes per axis
 //   k_nr_key       box key + arrival rank (histogram atomics)
 //   k_scan         exclusive scan of the histogram (shared with the sphere grid; clears it)
-//   k_nr_scatter   each agent's record into box order: FP32 box-relative geometry (mixed, 40 B,
-//                  the axis and radius as prepare wrote them) or FP64 end points (64 + 8 B)
+//   k_nr_scatter   each agent's records into box order: mixed, a dense 16 B box-relative binning
+//                  point + bound and a 32 B (axis, radius, id, mother) sector; FP64, end points
+//                  (64 + 8 B)
 //   k_nr_force     one thread per box-ordered slot: the 27 boxes around it (9 runs of 3), neighbour
 //                  count, contacts with the lever split, spring; own and passed-up shares in id
 //                  order, one 32 B (mixed) or 64 B (FP64) record per agent
 //   k_nr_update    id order: own share + daughters' passed-up shares (ascending daughter id),
-//                  capped displacement, new FP64 positions (ping-pong)
+//                  capped displacement (mixed: FP32, then one FP64 add per axis), new FP64
+//                  positions (ping-pong)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -413,11 +415,12 @@ struct alignas(64) NrOut64 {
   Dbl4 keep, pass;
 };
 
-// One thread per box-ordered slot t: agent i = C[t].x.  The 27 boxes around i's box are visited as 9
-// runs of 3 boxes adjacent in x, whose slots are contiguous.  Neighbours are counted in FP64 (R20;
-// the mixed kernel decides in FP32 outside a 2^-14 band around L^2 and re-tests inside it in FP64).
-// A candidate whose binning point is farther than the sum of the two half extents cannot touch and
-// skips the closest-point test.
+// One thread per box-ordered slot t: agent i = (id of slot t).  The 27 boxes around i's box are
+// visited as 9 runs of 3 boxes adjacent in x, whose slots are contiguous.  Neighbours are counted in
+// FP64 (R20; the mixed kernel decides in FP32 outside a 2^-14 band around L^2 and re-tests inside it
+// in FP64).  A candidate whose binning point is farther than the sum of the two half extents cannot
+// touch and skips the closest-point test.  The mixed kernel is held to 64 registers (twice the
+// resident warps of its natural allocation).
 template <bool MIXED>
 __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
     unsigned n, const unsigned* __restrict__ start, const unsigned* __restrict__ key,
