@@ -550,7 +550,7 @@ def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_ste
                              "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind,
                              "alg_bytes_per_agent": NEURITE_FORCE_BYTES_PER_AGENT,
-                             "traffic": None},
+                             "traffic": measured_traffic("nr_force", n)},
                 "step_roofline": {"bytes_per_agent_step": NEURITE_BYTES_PER_AGENT,
                                   "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                                   "frac": step_achieved / peak}})
