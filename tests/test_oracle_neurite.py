@@ -205,3 +205,29 @@ def test_sampled_step_equals_the_full_step():
     for a in "xyz":
         assert np.array_equal(smp[a], full[a][idx])
     assert smp["L"] == full["L"]
+
+
+def test_initial_pyramidal_cell_is_at_rest():
+    """The initial pyramidal cell of Sec. "Neuroscience use case": a 10 um soma with three basal and
+    one apical dendrite element of 0.5 um, attached at the soma surface.  At rest length the springs
+    carry no force, the roots are siblings (no contact with each other) and each root's soma is its
+    mother (no contact either), so nothing moves; stretching the apical element by 20 % pulls the
+    soma towards it and the element back, with equal and opposite forces."""
+    dirs = np.array([[0, 0, 1.0], [1.0, 0, -0.5], [-0.5, 0.87, -0.5], [-0.5, -0.87, -0.5]])
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    rows = [(0, 0, 0, 10.0, 0, -1, 0, 0, 0)]
+    for u in dirs:
+        p = 5.0 * u + 0.5 * u
+        rows.append((p[0], p[1], p[2], 1.0, 0.5, 0, 5.0 * u[0], 5.0 * u[1], 5.0 * u[2]))
+    inp = agents(rows)
+    r = step(inp)
+    assert np.allclose(r["force"], 0.0, atol=1e-12)
+    for a in "xyz":
+        assert np.allclose(r[a], inp[a], rtol=0, atol=1e-14)
+    stretched = dict(inp, z=inp["z"].copy())
+    stretched["z"][1] = 5.0 + 0.6  # apical element 0.6 um long
+    r = step(stretched)
+    T = KS * (0.6 - 0.5) / 0.5
+    assert np.allclose(r["force"][1], [0, 0, -T], atol=1e-12)
+    assert np.allclose(r["force"][0], [0, 0, T], atol=1e-12)
+    assert np.allclose(r["force"][2:], 0.0, atol=1e-12)
