@@ -76,7 +76,8 @@ int bdm_neurite_set_agents(bdm_neurite* s, size_t n, const double* x, const doub
 int bdm_neurite_step(bdm_neurite* s, int n);
 
 /* Synchronise and copy the state in id order.  Every pointer may be NULL.  n_out: agents; x/y/z:
- * positions (n each); neighbour_count: R20 counts of the last step (n); L_out: its radius L. */
+ * positions (n each); neighbour_count: R20 counts of the last step (n); L_out: its radius L.
+ * Before the first step after bdm_neurite_set_agents the counts and L read 0. */
 int bdm_neurite_get_state(bdm_neurite* s, size_t* n_out, double* x, double* y, double* z,
                           uint32_t* neighbour_count, double* L_out);
 
