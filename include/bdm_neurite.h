@@ -51,7 +51,7 @@ typedef struct bdm_neurite_params {
   double max_displacement;     /* cap on |displacement| per step                                 */
   double spring;               /* spring constant of an element (R17)                            */
   double interaction_radius;   /* lower bound of L (R20); 0 = the largest extent                 */
-  uint64_t capacity;           /* agents the handle can hold                                     */
+  uint64_t capacity;           /* agents the handle can hold (at most 2^31; 2^27 with BDM_MIXED) */
   uint64_t box_capacity;       /* grid boxes; 0 = 2 * capacity + 4096.  A step whose grid needs
                                   more fails with BDM_ENOMEM at the next synchronising call       */
   void* stream;                /* cudaStream_t, NULL = a stream the handle creates               */
