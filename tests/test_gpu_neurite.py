@@ -155,3 +155,35 @@ def test_full_size_forest_sampled_against_the_oracle():
     assert np.abs(d).max() < params["max_displacement"]
     assert np.abs(d.sum(0)).max() < 1e-6 * np.abs(d).sum()
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("change", [{"interaction_radius": 14.0}, {"max_displacement": 0.002},
+                                    {"spring": 0.0, "attraction": 0.0}])
+def test_radius_cap_and_law_variants(precision, change):
+    """A fixed radius above the largest extent (L = 14 um: more neighbours, same contacts), a cap
+    that most moving agents hit, and pure repulsion without springs."""
+    params, inp = synth.neuron_forest(12, 2000, side=45.0, seed=11)
+    params = dict(params, **change)
+    sim = make(params, precision)
+    sim.set_agents(inp)
+    cur = dict(inp)
+    for k in range(3):
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle_step(params, cur)
+        assert got["L"] == want["L"], k
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        for a in "xyz":
+            assert np.max(np.abs(got[a] - want[a])) < TOL[precision], (k, a)
+        prev = cur
+        cur = dict(cur, x=got["x"], y=got["y"], z=got["z"])
+    if "interaction_radius" in change:
+        assert got["L"] == 14.0
+    if "max_displacement" in change:
+        # the last oracle step started from `prev`; every displacement respects the cap, and many
+        # agents sit on it
+        moved = np.sqrt(sum((want[a] - prev[a]) ** 2 for a in "xyz"))
+        assert np.all(moved <= 0.002 * (1 + 1e-9))
+        assert np.mean(moved > 0.002 * (1 - 1e-6)) > 0.05
+    sim.close()
