@@ -181,6 +181,45 @@ def oracle_baseline(n_sample, steps=1):
             "kind": "oracle", "sample": s.describe(steps, secs)}
 
 
+def neurite_oracle_baseline(n_sample=20_000):
+    """The FP64 neurite oracle as it stands (every pair, no grid) for one step of a neuron forest of
+    n_sample agents at the benchmark's density and cell size."""
+    import oracle
+    scale = n_sample / 9_000_000
+    neurons = max(1, int(round(5000 * scale)))
+    side = 2000.0 * scale ** (1.0 / 3.0)
+    params, inp = synth.neuron_forest(neurons, n_sample, side=side)
+    t0 = time.perf_counter()
+    oracle.neurite_step(inp["x"], inp["y"], inp["z"], inp["diameter"], inp["rest"], inp["mother"],
+                        inp["ox"], inp["oy"], inp["oz"], params["dt"], params["repulsion"],
+                        params["attraction"], params["max_displacement"], params["spring"])
+    secs = time.perf_counter() - t0
+    return {"value": n_sample / secs, "unit": "agent-steps/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "1 step of a %d-agent forest at the same density (%d neurons, %.0f um cube), "
+                      "FP64 oracle over all pairs, OpenMP over agents; %.2f s"
+                      % (n_sample, neurons, side, secs)}
+
+
+def sir_oracle_baseline(runs=2, steps=20):
+    """The FP64/integer SIR oracle as it stands on `runs` runs of the ensemble, `steps` steps each."""
+    import oracle
+    ens = synth.sir_ensemble()[:runs]
+    secs, agents = 0.0, 0
+    for p, inp in ens:
+        sim = oracle.OracleSim(dict(p, sir_boxes=32))
+        sim.add_agents(inp["x"], inp["y"], inp["z"], sir_state=inp["sir_state"])
+        t0 = time.perf_counter()
+        sim.step(steps)
+        secs += time.perf_counter() - t0
+        agents += len(inp["x"])
+    return {"value": agents * steps / secs, "unit": "agent-steps/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d runs x %d persons of the ensemble, %d steps each, 32 boxes per axis, "
+                      "oracle (integer positions, one run at a time); %.2f s"
+                      % (runs, agents // max(1, runs), steps, secs)}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -425,7 +464,8 @@ def bench_ensemble(steps, baseline_runs):
             "sims_per_s": len(ens) / t_batch, "ms_per_step": 1e3 * t_batch / steps,
             "one_at_a_time_agent_steps_per_s": agents * steps / t_single,
             "speedup_vs_one_at_a_time": t_single / t_batch,
-            "one_at_a_time_sample_runs": baseline_runs}
+            "one_at_a_time_sample_runs": baseline_runs,
+            "cpu_baseline": sir_oracle_baseline()}
 
 
 def _event_time_ms(stream, fn):
@@ -510,11 +550,12 @@ NEURITE_FORCE_BYTES_PER_AGENT = 92  # own record (40) + spring and bound (16) + 
                                     # output record (32) written
 
 
-def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_steps=2):
+def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_steps=2,
+                  oracle_sample=20_000):
     """Neurite mechanics on the neuron forest (somata with apical and basal dendrite trees, the
     large pyramidal-cell run's 5000 cells and 9e6 agents), mixed precision: `steps` steps after
     `warmup`, timed on the device; per-kernel times from a separately profiled step; the FP64 check
-    path timed over `fp64_steps` steps for comparison."""
+    path timed over `fp64_steps` steps for comparison; the oracle on a bounded sample beside it."""
     from paper_2006_06775_gb300 import bdm
     # other sizes keep the density and the cells' size: neurons and cube side scale with n
     scale = n_agents / 9_000_000
@@ -561,6 +602,8 @@ def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_ste
         ms64 = _event_time_ms(sim.stream, lambda: sim.step(fp64_steps))
         sim.close()
         out["fp64_ms_per_step"] = ms64 / fp64_steps
+    if oracle_sample > 0:
+        out["cpu_baseline"] = neurite_oracle_baseline(oracle_sample)
     return out
 
 
