@@ -187,3 +187,37 @@ def test_radius_cap_and_law_variants(precision, change):
         assert np.all(moved <= 0.002 * (1 + 1e-9))
         assert np.mean(moved > 0.002 * (1 - 1e-6)) > 0.05
     sim.close()
+
+
+def _rows(rows):
+    a = np.array(rows, dtype=np.float64)
+    inp = {k: np.ascontiguousarray(a[:, i]) for i, k in
+           enumerate(("x", "y", "z", "diameter", "rest", "mother", "ox", "oy", "oz"))}
+    inp["mother"] = inp["mother"].astype(np.int32)
+    return inp
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_degenerate_geometry_one_step(precision):
+    """Coincident somata (counted, no force), a zero-length element (a point on its mother's distal
+    end), and two exactly parallel elements of different trees 0.8 um apart (closest points not
+    unique: both sides take the proximal end, s = 0)."""
+    params, _ = synth.neuron_forest(1, 1, seed=0)
+    inp = _rows([(0, 0, 0, 10, 0, -1, 0, 0, 0),          # soma A
+                 (0, 0, 0, 8, 0, -1, 0, 0, 0),           # soma B, coincident with A
+                 (30, 0, 0, 10, 0, -1, 0, 0, 0),         # soma C
+                 (39, 0, 0, 1.0, 4.0, 2, 5, 0, 0),       # element E1 on C: (35,0,0)-(39,0,0)
+                 (39, 0, 0, 1.0, 1.0, 3, 0, 0, 0),       # element E2 on E1: zero length at (39,0,0)
+                 (30, 0.8, 0, 10, 0, -1, 0, 0, 0),       # soma D overlapping C
+                 (39, 0.8, 0, 1.0, 4.0, 5, 5, 0, 0)])    # element F1 on D, parallel to E1
+    want = oracle_step(params, inp)
+    assert want["neighbour_count"][0] >= 1 and np.abs(want["force"]).max() > 0.0
+    sim = make(params, precision)
+    sim.set_agents(inp)
+    sim.step(1)
+    got = sim.get_state()
+    assert got["L"] == want["L"]
+    assert np.array_equal(got["neighbour_count"], want["neighbour_count"])
+    for a in "xyz":
+        assert np.max(np.abs(got[a] - want[a])) < TOL[precision], a
+    sim.close()
