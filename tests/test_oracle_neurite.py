@@ -231,3 +231,37 @@ def test_initial_pyramidal_cell_is_at_rest():
     assert np.allclose(r["force"][1], [0, 0, -T], atol=1e-12)
     assert np.allclose(r["force"][0], [0, 0, T], atol=1e-12)
     assert np.allclose(r["force"][2:], 0.0, atol=1e-12)
+
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+_coord = st.floats(-5.0, 5.0, allow_nan=False, allow_infinity=False)
+_vec = st.tuples(_coord, _coord, _coord).map(np.array)
+
+
+@settings(max_examples=150, deadline=None)
+@given(_vec, _vec, _vec, _vec)
+def test_closest_points_are_optimal_property(p0, u, q0, v):
+    """For any two segments the returned pair is no farther apart than the brute-force minimum over
+    the unit square (to its resolution) nor than any pair of end points."""
+    s, t = oracle.segment_closest(p0, u, q0, v)
+    assert 0.0 <= s <= 1.0 and 0.0 <= t <= 1.0
+    d = float(np.linalg.norm((p0 + s * u) - (q0 + t * v)))
+    ends = min(float(np.linalg.norm((p0 + a * u) - (q0 + b * v))) for a in (0, 1) for b in (0, 1))
+    assert d <= ends + 1e-12
+    assert d <= _brute_min(p0, u, q0, v, n=101) + 1e-9
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(0, 10_000), st.floats(15.0, 60.0), st.tuples(_coord, _coord, _coord))
+def test_forest_force_balance_and_translation_property(seed, side, shift):
+    """Random small forests: the total force vanishes, and translating every agent leaves each
+    force unchanged (to rounding at the forest's coordinates)."""
+    params, inp = synth.neuron_forest(3, 300, side=side, seed=seed)
+    r = step(inp)
+    f = r["force"]
+    assert np.abs(f.sum(0)).max() <= 1e-10 * max(1.0, np.abs(f).sum())
+    moved = dict(inp, x=inp["x"] + shift[0], y=inp["y"] + shift[1], z=inp["z"] + shift[2])
+    g = step(moved)["force"]
+    assert np.allclose(g, f, rtol=0, atol=1e-8 * max(1.0, np.abs(f).max()))
