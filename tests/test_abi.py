@@ -131,3 +131,18 @@ def test_neurite_struct_size_check(lib):
     rc = lib.bdm_neurite_create(ctypes.byref(p), ctypes.byref(h))
     assert rc in (bdm.BDM_OK, bdm.BDM_ECUDA), lib.bdm_neurite_last_error(h)
     lib.bdm_neurite_destroy(h)
+
+
+def test_headers_compile_as_plain_c(tmp_path):
+    """The boundary is plain C: every public header compiles as C99 (-pedantic, no warnings)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    heads = sorted(os.path.basename(h) for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    src = tmp_path / "headers.c"
+    src.write_text("".join('#include "%s"\n' % h for h in heads) + "int main(void) { return 0; }\n")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I" + os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
