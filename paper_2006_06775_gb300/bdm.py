@@ -539,7 +539,8 @@ NEURITE_FIELDS = ("x", "y", "z", "diameter", "rest", "mother", "ox", "oy", "oz")
 
 class Neurite:
     """One neurite-mechanics handle (somata and neurite elements).  params: dict as produced by
-    ``synth.neuron_forest`` plus ``precision`` ("mixed" or "fp64") and ``capacity``."""
+    ``synth.neuron_forest`` plus ``precision`` ("mixed" or "fp64"), ``capacity`` and optionally
+    ``box_capacity`` (default 8 * capacity + 4096 grid boxes)."""
 
     def __init__(self, params: dict, stream=None):
         import torch
@@ -552,7 +553,9 @@ class Neurite:
                   "interaction_radius"):
             setattr(p, k, float(self.params.get(k, 0.0)))
         p.capacity = int(self.params.get("capacity", 1 << 20))
-        p.box_capacity = int(self.params.get("box_capacity", 0))
+        # grid room for arbors that spread well beyond their somata (the library's own default,
+        # 2 * capacity + 4096 boxes, suits compact populations)
+        p.box_capacity = int(self.params.get("box_capacity", 0)) or 8 * p.capacity + 4096
         p.stream = self.stream.cuda_stream
         L = load()
         h = ctypes.c_void_p()
