@@ -207,27 +207,40 @@ def test_sampled_step_equals_the_full_step():
     assert smp["L"] == full["L"]
 
 
+def _pyramidal():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pyramidal_cell.json")
+    with open(path) as f:
+        return json.load(f)
+
+
 def test_initial_pyramidal_cell_is_at_rest():
-    """The initial pyramidal cell of Sec. "Neuroscience use case": a 10 um soma with three basal and
-    one apical dendrite element of 0.5 um, attached at the soma surface.  At rest length the springs
-    carry no force, the roots are siblings (no contact with each other) and each root's soma is its
-    mother (no contact either), so nothing moves; stretching the apical element by 20 % pulls the
-    soma towards it and the element back, with equal and opposite forces."""
+    """The initial pyramidal cell of Sec. "Neuroscience use case" (tests/golden/pyramidal_cell.json):
+    a 10 um soma with three basal and one apical dendrite element of 0.5 um, attached at the soma
+    surface.  At rest length the springs carry no force, the roots are siblings (no contact with
+    each other) and each root's soma is its mother (no contact either), so nothing moves; stretching
+    the apical element by 20 % pulls the soma towards it and the element back, with equal and
+    opposite forces."""
+    cell = _pyramidal()["initial_cell"]
+    ds, l0 = cell["soma_diameter_um"], cell["dendrite_length_um"]
+    assert (cell["apical_dendrites"], cell["basal_dendrites"]) == (1, 3)
+    rs = 0.5 * ds
     dirs = np.array([[0, 0, 1.0], [1.0, 0, -0.5], [-0.5, 0.87, -0.5], [-0.5, -0.87, -0.5]])
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
-    rows = [(0, 0, 0, 10.0, 0, -1, 0, 0, 0)]
+    rows = [(0, 0, 0, ds, 0, -1, 0, 0, 0)]
     for u in dirs:
-        p = 5.0 * u + 0.5 * u
-        rows.append((p[0], p[1], p[2], 1.0, 0.5, 0, 5.0 * u[0], 5.0 * u[1], 5.0 * u[2]))
+        p = rs * u + l0 * u
+        rows.append((p[0], p[1], p[2], 1.0, l0, 0, rs * u[0], rs * u[1], rs * u[2]))
     inp = agents(rows)
     r = step(inp)
     assert np.allclose(r["force"], 0.0, atol=1e-12)
     for a in "xyz":
         assert np.allclose(r[a], inp[a], rtol=0, atol=1e-14)
     stretched = dict(inp, z=inp["z"].copy())
-    stretched["z"][1] = 5.0 + 0.6  # apical element 0.6 um long
+    stretched["z"][1] = rs + 1.2 * l0  # apical element stretched by 20 %
     r = step(stretched)
-    T = KS * (0.6 - 0.5) / 0.5
+    T = KS * (1.2 * l0 - l0) / l0
     assert np.allclose(r["force"][1], [0, 0, -T], atol=1e-12)
     assert np.allclose(r["force"][0], [0, 0, T], atol=1e-12)
     assert np.allclose(r["force"][2:], 0.0, atol=1e-12)

@@ -133,7 +133,20 @@ def well_mixed_runs(N, L, nb, r, p, q, I0, steps, runs, seed):
     return np.array(hist, dtype=np.float64)  # (runs, steps+1, 3)
 
 
-@pytest.mark.parametrize("R0,TR", [(12.9, 8.0), (1.3, 4.1)])
+def _diseases():
+    """(R0, T_R) of the paper's two diseases, from tests/golden/sir_diseases.json."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sir_diseases.json")
+    with open(path) as f:
+        d = json.load(f)["diseases"]
+    return [(d[k]["R0"], d[k]["T_R_days"]) for k in ("measles", "influenza")]
+
+
+DISEASES = _diseases()
+
+
+@pytest.mark.parametrize("R0,TR", DISEASES)
 def test_well_mixed_expected_infections_unbiased(R0, TR):
     """Given (S, I) at step start, the expected number of new infections in the well-mixed model is
     S p (1 - (1 - v)^I) exactly, with v the lattice-ball fraction.  Per run, the summed surprises
@@ -154,7 +167,7 @@ def test_well_mixed_expected_infections_unbiased(R0, TR):
     assert abs(Dr.mean()) < 3.5 * Dr.std(ddof=1) / math.sqrt(len(Dr)) + 1.0
 
 
-@pytest.mark.parametrize("R0,TR", [(12.9, 8.0), (1.3, 4.1)])
+@pytest.mark.parametrize("R0,TR", DISEASES)
 def test_well_mixed_mean_follows_sir_curves(R0, TR):
     """Ensemble mean of the agent model (10 runs, as in the paper's Fig. 4) against (a) the discrete
     mean-field recurrence of the same model and (b) the Kermack-McKendrick ODE with R0 = beta/gamma,
