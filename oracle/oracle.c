@@ -580,7 +580,9 @@ static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
 /* Closest points of segments P(s) = P0 + s u and Q(t) = Q0 + t v, s, t in [0, 1] (a zero-length
  * segment is a point).  Minimises |P(s) - Q(t)|^2, a convex quadratic on the unit square: the
  * minimiser of the infinite lines clamped in s, then t optimal for that s, and if t had to be clamped
- * s optimal for the clamped t (Ericson, Real-Time Collision Detection, Sec. 5.1.9). */
+ * s optimal for the clamped t (Ericson, Real-Time Collision Detection, Sec. 5.1.9).  Segments with
+ * |u x v|^2 <= 1e-12 |u|^2 |v|^2 count as parallel (reading R18): s = 0, which is a tie for exactly
+ * parallel segments and within sin(angle) x length of the minimum otherwise. */
 void orc_segment_closest(const double P0[3], const double u[3], const double Q0[3],
                          const double v[3], double* s_out, double* t_out) {
   double w[3] = {P0[0] - Q0[0], P0[1] - Q0[1], P0[2] - Q0[2]};
