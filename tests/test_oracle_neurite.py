@@ -253,7 +253,7 @@ _coord = st.floats(-5.0, 5.0, allow_nan=False, allow_infinity=False)
 _vec = st.tuples(_coord, _coord, _coord).map(np.array)
 
 
-@settings(max_examples=300, deadline=None)
+@settings(max_examples=300, deadline=None, derandomize=True)
 @given(_vec, _vec, _vec, _vec)
 def test_closest_points_are_optimal_property(p0, u, q0, v):
     """For any two segments the returned pair is no farther apart than the brute-force minimum over
@@ -283,7 +283,7 @@ def test_parallel_rule_near_parallel_example():
     assert 0.0 < d - (1.0 - 1.192092896e-07) < 1e-6
 
 
-@settings(max_examples=25, deadline=None)
+@settings(max_examples=25, deadline=None, derandomize=True)
 @given(st.integers(0, 10_000), st.floats(15.0, 60.0), st.tuples(_coord, _coord, _coord))
 def test_forest_force_balance_and_translation_property(seed, side, shift):
     """Random small forests: the total force vanishes, and translating every agent leaves each
