@@ -578,34 +578,59 @@ static double dot3(const double a[3], const double b[3]) {
 static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
 
 /* Closest points of segments P(s) = P0 + s u and Q(t) = Q0 + t v, s, t in [0, 1] (a zero-length
- * segment is a point).  Minimises |P(s) - Q(t)|^2, a convex quadratic on the unit square: the
- * minimiser of the infinite lines clamped in s, then t optimal for that s, and if t had to be clamped
- * s optimal for the clamped t (Ericson, Real-Time Collision Detection, Sec. 5.1.9).  Segments with
- * |u x v|^2 <= 1e-12 |u|^2 |v|^2 count as parallel (reading R18): s = 0, which is a tie for exactly
- * parallel segments and within sin(angle) x length of the minimum otherwise. */
+ * segment is a point): the argmin of f(s, t) = |P(s) - Q(t)|^2 over the unit square, written out from
+ * its definition.  f is a convex quadratic, so its minimum over the square lies either at the
+ * stationary point of the two infinite lines (when that point is inside the square) or on one of
+ * the four edges, and on an edge at the clamped minimiser of a one-variable quadratic.  The
+ * candidates are therefore
+ *   s = 0 with t = clamp(E / C),        s = 1 with t = clamp((B + E) / C),
+ *   t = 0 with s = clamp(-D / A),       t = 1 with s = clamp((B - D) / A),
+ *   the stationary point s = (B E - C D) / den, t = (A E - B D) / den  (den = |u x v|^2 > 0),
+ * with w = P0 - Q0, A = u.u, B = u.v, C = v.v, D = u.w, E = v.w; each is scored by its own distance
+ * |P(s) - Q(t)|, evaluated directly.  Tie rule (reading R18): the first candidate in the order above
+ * whose distance is within 1e-12 (|u| + |v| + |w|) of the smallest; only parallel segments have
+ * tied candidates (their minimum is not unique), and the stationary point, listed last, then does
+ * not exist.  A point segment (A = 0 or C = 0) takes the clamped minimiser of the other parameter. */
+static double seg_pair_dist(const double P0[3], const double u[3], const double Q0[3],
+                            const double v[3], double s, double t) {
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = (P0[k] + s * u[k]) - (Q0[k] + t * v[k]);
+  return sqrt(dot3(d, d));
+}
+
 void orc_segment_closest(const double P0[3], const double u[3], const double Q0[3],
                          const double v[3], double* s_out, double* t_out) {
   double w[3] = {P0[0] - Q0[0], P0[1] - Q0[1], P0[2] - Q0[2]};
   double A = dot3(u, u), B = dot3(u, v), C = dot3(v, v), D = dot3(u, w), E = dot3(v, w);
-  double s, t;
-  if (A <= 0.0 && C <= 0.0) {
-    s = 0.0; t = 0.0;
-  } else if (A <= 0.0) {
-    s = 0.0; t = clamp01(E / C);
-  } else if (C <= 0.0) {
-    t = 0.0; s = clamp01(-D / A);
-  } else {
-    double den = A * C - B * B;
-    s = den > 1e-12 * (A * C) ? clamp01((B * E - C * D) / den) : 0.0;
-    t = (B * s + E) / C;
-    if (t < 0.0) {
-      t = 0.0; s = clamp01(-D / A);
-    } else if (t > 1.0) {
-      t = 1.0; s = clamp01((B - D) / A);
+  if (A <= 0.0 || C <= 0.0) {
+    *s_out = A <= 0.0 ? 0.0 : clamp01(-D / A);
+    *t_out = A <= 0.0 ? (C <= 0.0 ? 0.0 : clamp01(E / C)) : 0.0;
+    return;
+  }
+  double cs[5], ct[5];
+  int nc = 0;
+  cs[nc] = 0.0; ct[nc] = clamp01(E / C); ++nc;
+  cs[nc] = 1.0; ct[nc] = clamp01((B + E) / C); ++nc;
+  cs[nc] = clamp01(-D / A); ct[nc] = 0.0; ++nc;
+  cs[nc] = clamp01((B - D) / A); ct[nc] = 1.0; ++nc;
+  double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  double den = dot3(cr, cr);
+  if (den > 0.0) {
+    double ss = (B * E - C * D) / den, tt = (A * E - B * D) / den;
+    if (ss >= 0.0 && ss <= 1.0 && tt >= 0.0 && tt <= 1.0) {
+      cs[nc] = ss; ct[nc] = tt; ++nc;
     }
   }
-  *s_out = s;
-  *t_out = t;
+  double dist[5], dmin = INFINITY;
+  for (int c = 0; c < nc; ++c) {
+    dist[c] = seg_pair_dist(P0, u, Q0, v, cs[c], ct[c]);
+    if (dist[c] < dmin) dmin = dist[c];
+  }
+  double tol = 1e-12 * ((sqrt(A) + sqrt(C)) + sqrt(dot3(w, w)));
+  int pick = 0;
+  while (dist[pick] > dmin + tol) ++pick;
+  *s_out = cs[pick];
+  *t_out = ct[pick];
 }
 
 typedef struct {
