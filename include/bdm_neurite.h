@@ -11,9 +11,9 @@
  *       the proximal point q_a = p_{mother[a]} + o_a to the distal point p_a, radius d_a / 2;
  *   R17 spring: v = p_e - q_e, l = |v|, T = spring * (l - rest_e) / rest_e; the element's distal
  *       point takes -T v / l and its mother +T v / l;
- *   R18 contact: the closest points of the two bodies (segments with |u x v|^2 <= 1e-12
- *       |u|^2 |v|^2 count as parallel: the pair is taken at the first body's proximal end), then
- *       the sphere law F = k delta -
+ *   R18 contact: the closest points of the two bodies (the argmin of the distance between the
+ *       two axes; parallel axes, whose minimum is not unique, take the first of the edge
+ *       minimisers s = 0, s = 1, t = 0, t = 1 that attains it), then the sphere law F = k delta -
  *       gamma sqrt(rho delta) (delta = r_i + r_j - distance, rho = r_i r_j / (r_i + r_j)) along the
  *       line between them when delta > 0; an element at axial parameter s (0 proximal, 1 distal)
  *       keeps s of the force at its distal point and passes 1 - s to its mother;

@@ -73,10 +73,50 @@ __device__ __forceinline__ T clamp01(T v) {
   return v < T(0) ? T(0) : (v > T(1) ? T(1) : v);
 }
 
-// Closest points of segments P0 + s u and Q0 + t v (s, t in [0, 1]): the line minimiser clamped in
-// s, t optimal for that s, and s re-optimised if t was clamped (Ericson, Real-Time Collision
-// Detection, Sec. 5.1.9).  den = |u x v|^2; with FP32 it is taken from the cross product, which
-// keeps its accuracy for nearly parallel segments.
+// Closest points of segments P0 + s u and Q0 + t v (s, t in [0, 1]), the argmin of |P(s) - Q(t)|^2
+// on the unit square.  Non-parallel segments have a unique minimiser, found by clamping the line
+// minimiser in s, taking t optimal for that s, and re-optimising s if t was clamped (Ericson,
+// Real-Time Collision Detection, Sec. 5.1.9); den = |u x v|^2 (with FP32 from the cross product,
+// which keeps its accuracy for nearly parallel segments).  Segments with den <= 1e-12 |u|^2 |v|^2
+// are treated as parallel: the candidates are the four edge minimisers (s = 0, s = 1, t = 0,
+// t = 1, each with the clamped optimal other parameter), and the first in that order whose distance
+// is within a rounding tolerance of the smallest is taken.  That is reading R18's tie rule for
+// parallel segments, whose minimum is not unique.
+template <typename T>
+struct ParamPair {
+  T s, t;
+};
+
+// The parallel case, out of line (it is rare) with every argument a scalar, so the call passes
+// them in registers and the force kernel's register budget is not spent on it.
+template <typename T>
+__device__ __noinline__ ParamPair<T> closest_parallel(T w0, T w1, T w2, T u0, T u1, T u2, T v0,
+                                                      T v1, T v2, T A, T B, T C, T D, T E) {
+  T cs[4], ct[4], dist[4];
+  cs[0] = T(0); ct[0] = clamp01(E / C);
+  cs[1] = T(1); ct[1] = clamp01((B + E) / C);
+  cs[2] = clamp01(-D / A); ct[2] = T(0);
+  cs[3] = clamp01((B - D) / A); ct[3] = T(1);
+  T dmin = T(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const T d0 = (w0 + cs[c] * u0) - ct[c] * v0;
+    const T d1 = (w1 + cs[c] * u1) - ct[c] * v1;
+    const T d2 = (w2 + cs[c] * u2) - ct[c] * v2;
+    dist[c] = sqrt((d0 * d0 + d1 * d1) + d2 * d2);
+    dmin = c == 0 ? dist[c] : (dist[c] < dmin ? dist[c] : dmin);
+  }
+  const T tol = (sizeof(T) == 4 ? T(1e-5) : T(1e-12)) *
+                ((sqrt(A) + sqrt(C)) + sqrt((w0 * w0 + w1 * w1) + w2 * w2));
+  int pick = 3;
+#pragma unroll
+  for (int c = 2; c >= 0; --c) pick = dist[c] <= dmin + tol ? c : pick;
+  ParamPair<T> r;
+  r.s = pick == 0 ? cs[0] : (pick == 1 ? cs[1] : (pick == 2 ? cs[2] : cs[3]));
+  r.t = pick == 0 ? ct[0] : (pick == 1 ? ct[1] : (pick == 2 ? ct[2] : ct[3]));
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ void closest_params(const T P0[3], const T u[3], const T Q0[3],
                                                const T v[3], T& s, T& t) {
@@ -104,7 +144,14 @@ __device__ __forceinline__ void closest_params(const T P0[3], const T u[3], cons
     } else {
       den = A * C - B * B;
     }
-    s = den > T(1e-12) * (A * C) ? clamp01((B * E - C * D) / den) : T(0);
+    if (!(den > T(1e-12) * (A * C))) {
+      const ParamPair<T> r =
+          closest_parallel<T>(w0, w1, w2, u[0], u[1], u[2], v[0], v[1], v[2], A, B, C, D, E);
+      s = r.s;
+      t = r.t;
+      return;
+    }
+    s = clamp01((B * E - C * D) / den);
     t = (B * s + E) / C;
     if (t < T(0)) {
       t = T(0);

@@ -221,3 +221,31 @@ def test_degenerate_geometry_one_step(precision):
     for a in "xyz":
         assert np.max(np.abs(got[a] - want[a])) < TOL[precision], a
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parallel_elements_tie_rule_one_step(precision):
+    """Two exactly parallel elements of different trees, 0.8 um apart and overlapping along half
+    their length: E1 spans x in [35, 39], F1 x in [37, 41].  Their closest pair is not unique;
+    reading R18 takes the first edge minimiser that attains the distance: for E1 against F1 the
+    s = 1 edge (E1's distal end, F1 at t = 0.5), for F1 against E1 the s = 0 edge.  E1 therefore
+    keeps the whole contact force at its distal point and F1 passes all of it to its soma."""
+    params, _ = synth.neuron_forest(1, 1, seed=0)
+    inp = _rows([(30, 0, 0, 10, 0, -1, 0, 0, 0),         # soma C
+                 (39, 0, 0, 1.0, 4.0, 0, 5, 0, 0),       # element E1 on C: (35,0,0)-(39,0,0)
+                 (32, 0.8, 0, 10, 0, -1, 0, 0, 0),       # soma D
+                 (41, 0.8, 0, 1.0, 4.0, 2, 5, 0, 0)])    # element F1 on D: (37,0.8,0)-(41,0.8,0)
+    s, t = oracle.segment_closest([35, 0, 0], [4, 0, 0], [37, 0.8, 0], [4, 0, 0])
+    assert (s, t) == (1.0, 0.5)
+    want = oracle_step(params, inp)
+    assert np.abs(want["force"][3]).max() == 0.0  # F1 passed its whole share on (s = 0)
+    assert np.abs(want["force"][1]).max() > 0.0
+    sim = make(params, precision)
+    sim.set_agents(inp)
+    sim.step(1)
+    got = sim.get_state()
+    assert got["L"] == want["L"]
+    assert np.array_equal(got["neighbour_count"], want["neighbour_count"])
+    for a in "xyz":
+        assert np.max(np.abs(got[a] - want[a])) < TOL[precision], a
+    sim.close()
