@@ -276,8 +276,11 @@ int bdm_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out
  *   stream   cudaStream_t (NULL = legacy default stream); the call is asynchronous.
  * Allocates nothing: its scratch is a static device array of 65,536 doubles (512 KB per GPU that
  * loads the library), so grids needing more than 65,536 blocks of 32 x 8 x 16 voxels are rejected
- * with BDM_EINVAL (e.g. 512^3 uses 32,768).  The first call on a device looks up that array's
- * address once; make it before any stream capture.  All calls share the array: calls that overlap
+ * with BDM_EINVAL (e.g. 512^3 uses 32,768), as are grids beyond the launch limits (more than
+ * 65,535 blocks along y or z).  The first call on a device looks up that array's address once, in
+ * the device's primary context, and keeps it for the life of the process: make that call before any
+ * stream capture, and do not use the entry point after cudaDeviceReset or from a context other than
+ * the primary one (the array lives at another address there).  All calls share the array: calls that overlap
  * on the GPU race on it, so order them (one stream, or events).  Returns BDM_EINVAL for bad
  * arguments, BDM_ECUDA if the launch fails. */
 int bdm_diffusion_step_noalloc(const float* u, float* out, const int32_t grid_n[3],

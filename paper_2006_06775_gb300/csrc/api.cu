@@ -258,6 +258,9 @@ int check_params(bdm_sim* s, const bdm_params* p) {
     const double lam = (p->diffusion_coeff * p->dt_diffusion) / (p->voxel * p->voxel);
     if (lam > 1.0 / 6.0) return fail(s, BDM_EINVAL, "FTCS unstable: D dt / h^2 = %g > 1/6", lam);
     if (p->decay * p->dt_diffusion > 1.0) return fail(s, BDM_EINVAL, "decay * dt > 1");
+    if (!ftcs_launchable(p->grid_n))
+      return fail(s, BDM_EINVAL, "grid_n %d x %d x %d exceeds the FTCS launch limits", p->grid_n[0],
+                  p->grid_n[1], p->grid_n[2]);
   }
   return BDM_OK;
 }

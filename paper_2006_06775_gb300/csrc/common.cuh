@@ -325,7 +325,10 @@ void launch_prepare_agents(cudaStream_t s, unsigned n0, unsigned n, const double
 // diffusion.cu
 void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], float lambda,
                  float mu_dt, double* partials, DevGrid* g);
-int ftcs_partials_needed(const int dims[3]);
+// Block partials of one FTCS step (an upper bound for both kernels), in 64-bit arithmetic.
+long long ftcs_partials_needed(const int dims[3]);
+// The FTCS launches fit the grid-dimension limits and their block count fits an int.
+bool ftcs_launchable(const int dims[3]);
 void launch_grid_mass(cudaStream_t s, const float* u, const int dims[3], double* partials, DevGrid* g);
 void launch_ftcs_mass_to(cudaStream_t s, const float* u, float* out, const int dims[3],
                          float lambda, float mu_dt, double* partials, double* mass);

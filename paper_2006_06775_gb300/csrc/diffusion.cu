@@ -183,8 +183,16 @@ __global__ void __launch_bounds__(kFX* kFY) k_grid_partials(const float* __restr
   }
 }
 
-int ftcs_partials_needed(const int dims[3]) {
-  return ((dims[0] + kFX - 1) / kFX) * ((dims[1] + kFY - 1) / kFY) * ((dims[2] + kFZ - 1) / kFZ);
+long long ftcs_partials_needed(const int dims[3]) {
+  return (long long)((dims[0] + (long long)kFX - 1) / kFX) * ((dims[1] + (long long)kFY - 1) / kFY) *
+         ((dims[2] + (long long)kFZ - 1) / kFZ);
+}
+
+bool ftcs_launchable(const int dims[3]) {
+  // grid.y and grid.z of both FTCS kernels, and the block count the mass kernel takes as an int
+  return dims[0] > 0 && dims[1] > 0 && dims[2] > 0 &&
+         (dims[1] + (long long)kFY - 1) / kFY <= 65535 &&
+         (dims[2] + (long long)kFZ - 1) / kFZ <= 65535 && ftcs_partials_needed(dims) <= INT32_MAX;
 }
 
 // One FTCS step into `out` with the block partials of its mass; returns how many partials it wrote
@@ -213,7 +221,7 @@ void launch_ftcs(cudaStream_t s, const float* u, float* out, const int dims[3], 
 void launch_grid_mass(cudaStream_t s, const float* u, const int dims[3], double* partials, DevGrid* g) {
   dim3 grid((dims[0] + kFX - 1) / kFX, (dims[1] + kFY - 1) / kFY, (dims[2] + kFZ - 1) / kFZ);
   k_grid_partials<<<grid, dim3(kFX, kFY), 0, s>>>(u, dims[0], dims[1], dims[2], partials);
-  k_mass<<<1, 1024, 0, s>>>(partials, ftcs_partials_needed(dims), g);
+  k_mass<<<1, 1024, 0, s>>>(partials, (int)ftcs_partials_needed(dims), g);
 }
 
 void launch_ftcs_mass_to(cudaStream_t s, const float* u, float* out, const int dims[3],

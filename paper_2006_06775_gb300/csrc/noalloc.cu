@@ -31,7 +31,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_partials_ptr[kMaxDevices] = {};
 
-// Device address of the static scratch array for the current device; looked up once per device.
+// Device address of the static scratch array for the current device; looked up once per device (in
+// its primary context, which is what the runtime API makes current) and kept for the life of the
+// process.  The address is not valid after cudaDeviceReset or in another context.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -61,7 +63,9 @@ extern "C" int bdm_diffusion_step_noalloc(const float* u, float* out, const int3
   const double lam = (diffusion_coeff * dt_diffusion) / (voxel * voxel);
   if (lam > 1.0 / 6.0 || decay * dt_diffusion > 1.0) return BDM_EINVAL;
   const int dims[3] = {grid_n[0], grid_n[1], grid_n[2]};
-  if (bdm::ftcs_partials_needed(dims) > bdm::kNoAllocMaxPartials) return BDM_EINVAL;
+  // block count in 64-bit arithmetic (no wrap-around for huge extents), within the launch limits
+  if (!bdm::ftcs_launchable(dims) || bdm::ftcs_partials_needed(dims) > bdm::kNoAllocMaxPartials)
+    return BDM_EINVAL;
   void* partials = nullptr;
   if (scratch_address(&partials) != cudaSuccess) {
     cudaGetLastError();

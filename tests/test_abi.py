@@ -146,3 +146,24 @@ def test_headers_compile_as_plain_c(tmp_path):
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I" + os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_noalloc_rejects_wrapping_and_unlaunchable_grids_on_cpu(lib):
+    """The allocation-free diffusion step refuses, before any CUDA call, grids whose block count
+    would wrap a 32-bit product (2^31 - 1 x 512 x 1 gives 2^26 * 64 = 2^32 blocks of 32 x 8 x 16)
+    and grids beyond the launch limits (more than 65,535 blocks along y), so no pointer is touched."""
+    for shape in ((2**31 - 1, 512, 1), (8, 8 * 65536, 16), (8, 8, 16 * 65536)):
+        rc = bdm.bdm_diffusion_step_noalloc(1 << 20, 2 << 20, shape, 0.4, 1.0, 10.0, 0.01)
+        assert rc == bdm.BDM_EINVAL, shape
+
+
+def test_create_rejects_unlaunchable_diffusion_grid(lib):
+    p = bdm.make_params({"kind": "mechanics", "precision": "mixed", "dt": 0.01, "repulsion": 2.0,
+                         "attraction": 1.0, "max_displacement": 3.0, "diffusion_enabled": 1,
+                         "grid_n": (8, 8 * 65536, 16), "voxel": 10.0, "diffusion_coeff": 0.4,
+                         "dt_diffusion": 1.0, "decay": 0.01})
+    h = ctypes.c_void_p()
+    rc = lib.bdm_create(ctypes.byref(p), ctypes.byref(h))
+    assert rc == bdm.BDM_EINVAL
+    assert b"launch limits" in lib.bdm_last_error(h)
+    lib.bdm_destroy(h)
