@@ -345,13 +345,21 @@ def run_ours(args):
     alg_bytes = bytes_pa * n
     achieved_gb = alg_bytes / (force_ms * 1e-3) / 1e9
     mech_ms = sum(v[1] for k, v in ktimes.items() if k != "ftcs") / args.steps
-    step_bytes = STEP_BYTES_PER_AGENT(boxes_per_agent) * n + 8.0 * 512 ** 3
+    # The step's algorithmic bytes count the per-step rebuild the method defines (box = interaction
+    # radius R, the largest diameter), whatever cadence runs: 4 S + 8 B_R per agent + 8 per voxel.
+    R = float(np.max(inp["diameter"]))
+    dims_R = [int(np.floor((float(np.max(inp[a])) - float(np.min(inp[a]))) / R)) + 1 for a in "xyz"]
+    boxes_per_agent_R = float(np.prod(dims_R, dtype=np.float64)) / n
+    step_bpa = STEP_BYTES_PER_AGENT(boxes_per_agent_R)
+    step_bytes = step_bpa * n + 8.0 * 512 ** 3
     step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": fkernel, "achieved": achieved_gb, "peak": peak,
                 "unit": "GB/s", "frac": achieved_gb / peak, "traffic": measured_traffic(fkernel, n),
                 "peak_kind": peak_kind, "alg_bytes_per_agent": bytes_pa,
                 "alg_flop_per_byte": flop_pa / bytes_pa,
-                "dominant_kernel_by_time": dom,
+                "dominant_kernel_by_time": dom, "kernel_ms": force_ms,
+                "step_ms": ms_per_step, "step_alg_bytes": step_bytes,
+                "step_bytes_per_agent": step_bpa, "step_frac": step_achieved / peak,
                 "fp32": {"achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved_tf / FP32_PEAK_TFLOPS, "alg_flop_per_agent": flop_pa,
                          "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz)"}}
@@ -402,10 +410,13 @@ def run_ours(args):
                                         "grid_rebuilds_in_timed_steps": rebuilds_timed,
                                         "list_entries_per_agent": (st1["list_entries"] / n
                                                                    if skin > 0.0 else None)},
+                       "skin_um": skin, "grid_rebuilds_timed": rebuilds_timed,
+                       "list_entries_per_agent": (st1["list_entries"] / n if skin > 0.0 else 0.0),
+                       "boxes_per_agent_R": round(boxes_per_agent_R, 4),
                        "cache": "inputs larger than L2 (agent state ~12 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
-            "step_roofline": {"bytes_per_agent_step": STEP_BYTES_PER_AGENT(boxes_per_agent),
+            "step_roofline": {"bytes_per_agent_step": step_bpa,
                               "diffusion_bytes_per_step": 8 * 512 ** 3,
                               "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                               "frac": step_achieved / peak, "nominal_peak": 7900.0,
