@@ -170,3 +170,77 @@ def test_stationary_skip_matches_oracle_every_step():
     params = dict(params, interaction_radius=R, box_length=R + 2.5, skin=2.5, skip_stationary=1)
     worst, rebuilds = run_teacher_forced(params, inp, 10)
     assert worst < 2e-5, worst
+
+
+def _bench_knobs(n, params, inp):
+    """The tuned sort cadence the benchmark runs at this size on GB300 (tuned.json)."""
+    from paper_2006_06775_gb300 import tune
+    cache = tune.TuneCache(tune.__file__.replace("tune.py", "tuned.json"))
+    sig = tune.workload_signature(params, n, inp["side"] ** 3)
+    knobs = cache.get(sig, "NVIDIA GB300")
+    assert knobs is not None and knobs["skin"] > 0.0, "the benchmark's configuration uses lists"
+    return knobs
+
+
+def _grid_boxes(x, y, z, st):
+    """Box id of every agent on the grid the state reports (reading R5), from the centres."""
+    box = np.zeros(len(x), np.int64)
+    mult = 1
+    for a, c in enumerate((x, y, z)):
+        q = np.rint(c * 1048576.0).astype(np.int64)
+        assert q.min() == st["grid_origin_q"][a]
+        b = (q - q.min()) // st["grid_box_q"]
+        assert b.max() == st["grid_dims"][a] - 1
+        box += b * mult
+        mult *= int(st["grid_dims"][a])
+    return box
+
+
+def test_full_size_timed_configuration_sampled():
+    """The benchmark's timed configuration at its full size: 10^8 agents with the tuned skin (grid
+    box R + skin), 14 steps from the fresh packing, which rebuild the grid at least twice and
+    evaluate the lists on at least five steps.  Every step is teacher-forced: from the GPU's own
+    state, every agent's box id against the step's grid, and sampled agents' neighbour counts (bit
+    exact) and displacements (within 2e-5 um) against the oracle run on sub-cubes that contain their
+    whole neighbourhood.  (The co-stepped substance grid of the benchmark does not enter the
+    mechanics and is left out.)"""
+    n = 100_000_000
+    params, inp = synth.large_mechanics(n=n, seed=2, with_grid=False)
+    from paper_2006_06775_gb300 import tune
+    params = tune.mechanics_params(params, inp, _bench_knobs(n, params, inp))
+    sim = bdm.Sim(params)
+    sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+    d = inp["diameter"]
+    R = float(d.max())
+    side = inp["side"]
+    g = synth.rng(98)
+    H = 60.0
+    x, y, z = inp["x"], inp["y"], inp["z"]
+    checked = 0
+    rebuilds0 = sim.get_state(fields=())["grid_rebuilds"]
+    kinds = []
+    for k in range(14):
+        before = sim.get_state(fields=())["grid_rebuilds"]
+        sim.step(1)
+        st = sim.get_state(fields=("x", "y", "z", "neighbour_count", "box_id"))
+        kinds.append(st["grid_rebuilds"] > before)
+        assert np.array_equal(_grid_boxes(x, y, z, st), st["box_id"].astype(np.int64)), k
+        for _ in range(3):
+            c = g.uniform(H + 10.0, side - H - 10.0, 3)
+            outer = (np.abs(x - c[0]) < H) & (np.abs(y - c[1]) < H) & (np.abs(z - c[2]) < H)
+            idx = np.nonzero(outer)[0]
+            sub = oracle.mech_step(x[idx], y[idx], z[idx], d[idx], params["dt"],
+                                   params["repulsion"], params["attraction"],
+                                   params["max_displacement"], interaction_radius=R)
+            inner = ((np.abs(x[idx] - c[0]) < H - 2 * R) & (np.abs(y[idx] - c[1]) < H - 2 * R) &
+                     (np.abs(z[idx] - c[2]) < H - 2 * R))
+            ii = idx[inner]
+            assert np.array_equal(st["neighbour_count"][ii], sub["neighbour_count"][inner]), k
+            for a, c0 in (("x", x), ("y", y), ("z", z)):
+                np.testing.assert_allclose(st[a][ii] - c0[ii], sub[a][inner] - c0[ii], atol=2e-5)
+            checked += len(ii)
+        x, y, z = st["x"], st["y"], st["z"]
+    assert sim.get_state(fields=())["grid_rebuilds"] - rebuilds0 >= 2
+    assert sum(kinds) >= 2 and len(kinds) - sum(kinds) >= 5, kinds
+    assert checked > 5000
+    sim.close()
