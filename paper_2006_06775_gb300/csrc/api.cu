@@ -380,7 +380,10 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
           (rc = dalloc_n(s, &b.pset[1].y, C)) || (rc = dalloc_n(s, &b.pset[1].z, C)) ||
           (rc = dalloc_n(s, &b.p4set[1], C)))
         return rc;
-      if (p.skip_stationary && ((rc = dalloc_n(s, &b.moved[0], C)) || (rc = dalloc_n(s, &b.moved[1], C))))
+      const size_t ngrp = (C + 31) / 32;
+      if (p.skip_stationary && ((rc = dalloc_n(s, &b.moved[0], C)) || (rc = dalloc_n(s, &b.moved[1], C)) ||
+                                (rc = dalloc_n(s, &b.wmoved[0], ngrp)) || (rc = dalloc_n(s, &b.wmoved[1], ngrp)) ||
+                                (rc = dalloc_n(s, &b.wbounds, ngrp))))
         return rc;
       CK(cudaMemsetAsync(b.list_n, 0, sizeof(unsigned) * C, s->stream));
       CK(cudaMemsetAsync(b.disp, 0, sizeof(float) * C, s->stream));

@@ -240,6 +240,12 @@ __device__ __forceinline__ void block_commit_bounds(unsigned long long mn[3], un
 // ---- launch wrappers (defined in the .cu files, called by the C ABI layer) ---------------------
 namespace bdm {
 
+struct WarpBounds {              // bounds of a warp-sized group of agents (stationary skip)
+  unsigned long long mn[3], mx[3];  // order-preserving encodings of the per-axis min / max centre
+  unsigned md;                      // float bits of the largest diameter
+  float dm;                         // largest move since the last rebuild
+};
+
 struct AgentArrays {             // one SoA buffer of agents
   double *x, *y, *z;
   float* diam;
@@ -267,6 +273,10 @@ struct MechBuffers {
   unsigned* list_n;
   float* disp;                   // |moves| of each agent since the last rebuild
   unsigned char* moved[2];       // 1 if the agent's displacement was nonzero (alternate like pset)
+  // stationary skip: 1 if any agent of a warp-sized group moved (alternate like pset), and each
+  // group's bounds, largest diameter and move since the rebuild as of its last evaluation
+  unsigned char* wmoved[2];
+  struct WarpBounds* wbounds;
 };
 
 // grid.cu

@@ -388,7 +388,8 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     double* __restrict__ oz, float4* __restrict__ op4, unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, unsigned* __restrict__ list, unsigned* __restrict__ list_n,
     float* __restrict__ disp, unsigned* __restrict__ nbr, const unsigned char* __restrict__ mprev,
-    unsigned char* __restrict__ mnext, DevGrid* g, MechConsts c) {
+    unsigned char* __restrict__ mnext, const unsigned char* __restrict__ wprev,
+    unsigned char* __restrict__ wnext, WarpBounds* __restrict__ wcache, DevGrid* g, MechConsts c) {
   // BUILD: the walk with forces, only on a rebuild step whose lists overflowed; otherwise the lists
   // (built by k_list_build on a rebuild step) give the forces
   if (BUILD ? !(g->rebuild && g->list_overflow) : g->list_overflow != 0u) return;
@@ -442,8 +443,10 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   };
   unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   int buf = 0;
-  // stationary agents are looked for only on list steps (a rebuild renumbers the agents)
-  const bool look = SKIP && !BUILD && !rb;
+  // stationary agents are looked for only from the second list step after a rebuild: a rebuild
+  // renumbers the agents, and it writes only one of the two position sets, so the other holds the
+  // agents' centres again only once the first list step has written it
+  const bool look = SKIP && !BUILD && !rb && g->since_rebuild >= 2u;
   if constexpr (!BUILD) {
     if (i < n) prefetch(i, 0);
     cp_async_commit();
@@ -452,7 +455,48 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     float4 pi;
     bool still = false;
     const bool own_still = look && __ldg(mprev + i) == 0;
-    if constexpr (BUILD) {
+    double x0 = 0.0, y0 = 0.0, z0 = 0.0;  // this agent's step-start centre
+    float dprev = 0.f;
+    if constexpr (SKIP && !BUILD) {
+      // stationary: this agent kept its position in the previous step and so did every agent of
+      // the warps its listed neighbours belong to, so its evaluation would repeat (zero
+      // displacement, the same count).  A warp whose agents are all stationary is skipped whole:
+      // both position sets already hold its centres and offsets (they did not move), so nothing is
+      // rewritten, and its bounds come from the warp's cache.
+      if (i + stride < n) prefetch(i + stride, buf ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();  // this agent's prefetch (issued one iteration earlier) has landed
+      pi = s_pi[buf][t];
+      if (own_still) {
+        const unsigned ml = s_m[buf][t];
+        still = true;
+        for (unsigned k = 0; k < ml && still; ++k) {
+          const unsigned v = k < 4u ? s_v[buf][k][t] : __ldg(list + list_at(i, k));
+          still = __ldg(wprev + (v >> 10)) == 0;  // the warp of agent v >> 5
+        }
+      }
+      const unsigned am = __activemask();
+      if (look && __all_sync(am, still)) {
+        mnext[i] = 0;
+        if ((t & 31) == 0) {
+          const WarpBounds wb = wcache[i >> 5];
+          wnext[i >> 5] = 0;
+          for (int a = 0; a < 3; ++a) {
+            s_mn[a][t] = wb.mn[a] < s_mn[a][t] ? wb.mn[a] : s_mn[a][t];
+            s_mx[a][t] = wb.mx[a] > s_mx[a][t] ? wb.mx[a] : s_mx[a][t];
+          }
+          s_md[t] = wb.md > s_md[t] ? wb.md : s_md[t];
+          s_dm[t] = fmaxf(s_dm[t], wb.dm);
+          atomicAdd(&s_skip, (unsigned)__popc(am));
+        }
+        buf ^= 1;
+        continue;
+      }
+      x0 = sx[i];  // evaluated: centre and move requested now, used after the force loop
+      y0 = sy[i];
+      z0 = sz[i];
+      dprev = disp[i];
+    } else if constexpr (BUILD) {
       pi = __ldg(p4 + i);
     } else {
       cp_async_n<8>(&s_c[0][t], sx + i);
@@ -547,15 +591,6 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
       // does not wait on one dependent load pair per entry
       // stationary: this agent and every listed neighbour kept their position in the previous step,
       // so the evaluation would repeat (zero displacement, the same count): it is skipped
-      if (SKIP && own_still) {
-        const unsigned ml = s_m[buf][t];
-        still = true;
-        for (unsigned k = 0; k < ml && still; ++k) {
-          const unsigned v = k < 4u ? s_v[buf][k][t] : __ldg(list + list_at(i, k));
-          still = __ldg(mprev + (v >> 5)) == 0;
-        }
-        if (still) atomicAdd(&s_skip, 1u);
-      }
       const unsigned m = still ? 0u : s_m[buf][t];
       // the warp runs to its longest list (a uniform bound: no lane leaves the loop early; slots
       // past a lane's list are evaluated as far away and add nothing)
@@ -615,17 +650,18 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
       const float f = c.capf * rsqrtf(n2);
       Dx *= f; Dy *= f; Dz *= f;
     }
-    if (!still) nbr[i] = cnt;  // a skipped agent keeps the previous step's count
-    if (mnext) mnext[i] = (Dx != 0.f || Dy != 0.f || Dz != 0.f) ? 1 : 0;
+    if (!still) nbr[i] = cnt;  // a stationary agent keeps the previous step's count
+    const bool moved = Dx != 0.f || Dy != 0.f || Dz != 0.f;
+    if (mnext) mnext[i] = moved ? 1 : 0;
     // update: FP64 centre += displacement (exact conversion, one FP64 add), FP32 offset +=
     // displacement, move since the rebuild (a list step's box ids are derived on read-out:
     // k_readout_box)
-    double x0, y0, z0;
-    float dprev = 0.f;
     if constexpr (BUILD) {
       x0 = sx[i];
       y0 = sy[i];
       z0 = sz[i];
+    } else if constexpr (SKIP) {
+      buf ^= 1;
     } else {
       cp_async_wait<1>();  // this agent's centre and move (the newest group is the next prefetch)
       x0 = s_c[0][t];
@@ -653,6 +689,45 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     s_mx[2][t] = e2 > s_mx[2][t] ? e2 : s_mx[2][t];
     const unsigned dbits = __float_as_uint(2.0f * pi.w);
     s_md[t] = dbits > s_md[t] ? dbits : s_md[t];
+    if constexpr (SKIP && !BUILD) {
+      // the warp's cache: bounds of its new centres, its largest diameter and move (lanes past n
+      // have left the loop; the active lanes are a prefix of the warp)
+      const unsigned am = __activemask();
+      const int lane = t & 31, na = __popc(am);
+      unsigned long long wmn[3] = {e0, e1, e2}, wmx[3] = {e0, e1, e2};
+      unsigned wmd = dbits;
+      float wdm = D;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const bool in = lane + o < na;
+        for (int a = 0; a < 3; ++a) {
+          const unsigned long long u = __shfl_down_sync(am, wmn[a], o);
+          const unsigned long long v = __shfl_down_sync(am, wmx[a], o);
+          if (in) {
+            wmn[a] = u < wmn[a] ? u : wmn[a];
+            wmx[a] = v > wmx[a] ? v : wmx[a];
+          }
+        }
+        const unsigned ud = __shfl_down_sync(am, wmd, o);
+        const float ug = __shfl_down_sync(am, wdm, o);
+        if (in) {
+          wmd = ud > wmd ? ud : wmd;
+          wdm = fmaxf(wdm, ug);
+        }
+      }
+      const unsigned anymoved = __ballot_sync(am, moved);
+      if (lane == 0) {
+        WarpBounds wb;
+        for (int a = 0; a < 3; ++a) {
+          wb.mn[a] = wmn[a];
+          wb.mx[a] = wmx[a];
+        }
+        wb.md = wmd;
+        wb.dm = wdm;
+        wcache[i >> 5] = wb;
+        wnext[i >> 5] = anymoved ? 1 : 0;
+      }
+    }
   }
   if constexpr (!BUILD) cp_async_wait<0>();
   __shared__ unsigned s_dmax;
@@ -1310,18 +1385,20 @@ void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g
     k_force_skin<true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
                                                    b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
                                                    b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
-                                                   b.moved[cur], b.moved[cur ^ 1], g, c);
+                                                   b.moved[cur], b.moved[cur ^ 1], b.wmoved[cur],
+                                                   b.wmoved[cur ^ 1], b.wbounds, g, c);
   else if (c.skip_stationary)
     k_force_skin<false, true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y,
                                                           P.z, b.p4set[cur], N.x, N.y, N.z,
                                                           b.p4set[cur ^ 1], b.skey, b.start, b.list,
                                                           b.list_n, b.disp, b.nbr, b.moved[cur],
-                                                          b.moved[cur ^ 1], g, c);
+                                                          b.moved[cur ^ 1], b.wmoved[cur],
+                                                          b.wmoved[cur ^ 1], b.wbounds, g, c);
   else
     k_force_skin<false><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
                                                     b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
                                                     b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
-                                                    nullptr, nullptr, g, c);
+                                                    nullptr, nullptr, nullptr, nullptr, nullptr, g, c);
 }
 
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
