@@ -256,6 +256,45 @@ int bdm_batch_counts(bdm_batch* b, uint32_t* out, int max_steps, int* steps);
 void bdm_batch_destroy(bdm_batch* b);
 const char* bdm_batch_last_error(const bdm_batch* b);
 
+/* ---- Batched mechanics (served simulations) --------------------------------------------------- */
+/* A pool of simulation slots for the plain sphere mechanics (Sec. "Simulation concepts": every step
+ * the uniform-grid rebuild, the 27-box neighbour search, the force and the capped update; readings
+ * R1-R6).  A slot holds one simulation of up to slot_capacity agents with its own parameters and
+ * step target; simulations are loaded into free slots and released between steps at any time
+ * (continuous admission).  Every step advances all active slots together in nine launches,
+ * whatever the number of simulations: each kernel covers a work list of (slot, 256-agent tile)
+ * pairs, and each slot keeps its own grid, agent range and box range.  Steps are captured into a
+ * CUDA graph per step count.  Each slot computes what a single handle (bdm_create) computes for the
+ * same simulation, which rebuilds the grid every step, bit for bit on both paths (the mixed path's
+ * per-pair FP32 operations are explicitly rounded, so no kernel contracts them differently).
+ *   precision             BDM_FP64 or BDM_MIXED (every slot)
+ *   slots, slot_capacity  pool shape, slots x slot_capacity < 2^31 agents; allocated here: about
+ *                         100 B per agent place and 8 B per box place, 2 slot_capacity + 4096 box
+ *                         places per slot
+ *   stream                cudaStream_t, NULL = a stream the pool creates */
+typedef struct bdm_mbatch bdm_mbatch;
+int bdm_mbatch_create(int precision, int slots, size_t slot_capacity, void* stream,
+                      bdm_mbatch** out);
+/* Load a simulation into free slot `slot`: its parameters p (kind BDM_MECHANICS, the pool's
+ * precision, no skin, growth, diffusion or oncology behaviours), its n agents (HOST arrays, um;
+ * 1 <= n <= slot_capacity; ids 0 .. n - 1 in this order) and the number of steps it runs.  Waits for
+ * the pool's stream.  BDM_ESTATE if the slot is occupied; BDM_EINVAL for bad parameters or agents
+ * (a diameter <= 0 or |position| >= 1e9 um). */
+int bdm_mbatch_load(bdm_mbatch* b, int slot, const bdm_params* p, size_t n, const double* x,
+                    const double* y, const double* z, const float* diameter, int steps);
+/* Advance every active slot by n steps (a slot stops at its step target); asynchronous. */
+int bdm_mbatch_step(bdm_mbatch* b, int n);
+/* Steps completed by each slot into steps_done[slots] (-1 for a free slot).  Waits for the stream. */
+int bdm_mbatch_poll(bdm_mbatch* b, int32_t* steps_done);
+/* One slot's state in agent-id order (box ids on the slot's grid of its last step), like
+ * bdm_get_state; grid_rebuilds = the slot's steps.  Waits for the stream.  BDM_ENOMEM if the slot's
+ * grid needed more boxes than it holds, BDM_ESTATE for another grid failure. */
+int bdm_mbatch_get_state(bdm_mbatch* b, int slot, bdm_state* st);
+/* Free a slot for the next simulation (its state is discarded).  Waits for the stream. */
+int bdm_mbatch_release(bdm_mbatch* b, int slot);
+void bdm_mbatch_destroy(bdm_mbatch* b);
+const char* bdm_mbatch_last_error(const bdm_mbatch* b);
+
 /* ---- Utility ----------------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind division axes and the SIR
  * behaviours, evaluated by the library's device code.  ctr: n x 4 words, key: n x 2 words, out:

@@ -130,6 +130,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.bdm_batch_destroy.restype = None
     L.bdm_batch_last_error.argtypes = [vp]
     L.bdm_batch_last_error.restype = ctypes.c_char_p
+    L.bdm_mbatch_create.argtypes = [i32, i32, sz, vp, ctypes.POINTER(vp)]
+    L.bdm_mbatch_load.argtypes = [vp, i32, ctypes.POINTER(Params), sz, vp, vp, vp, vp, i32]
+    L.bdm_mbatch_step.argtypes = [vp, i32]
+    L.bdm_mbatch_poll.argtypes = [vp, vp]
+    L.bdm_mbatch_get_state.argtypes = [vp, i32, ctypes.POINTER(State)]
+    L.bdm_mbatch_release.argtypes = [vp, i32]
+    L.bdm_mbatch_destroy.argtypes = [vp]
+    L.bdm_mbatch_destroy.restype = None
+    L.bdm_mbatch_last_error.argtypes = [vp]
+    L.bdm_mbatch_last_error.restype = ctypes.c_char_p
     L.bdm_neurite_create.argtypes = [ctypes.POINTER(NeuriteParams), ctypes.POINTER(vp)]
     L.bdm_neurite_set_agents.argtypes = [vp, sz] + [vp] * 9
     L.bdm_neurite_step.argtypes = [vp, i32]
@@ -378,6 +388,77 @@ def bdm_batch_counts(b, runs, max_steps):
 def bdm_batch_destroy(b):
     if b:
         load().bdm_batch_destroy(b)
+
+
+class MechBatch:
+    """Pool of mechanics simulation slots advanced together (bdm_mbatch_*): load a simulation into a
+    free slot with its step target, step the pool, poll, read a finished slot, release it."""
+
+    def __init__(self, precision="mixed", slots=64, slot_capacity=32768, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.slots = int(slots)
+        self.slot_capacity = int(slot_capacity)
+        prec = {"fp64": 0, "mixed": 1}[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        rc = load().bdm_mbatch_create(prec, self.slots, self.slot_capacity,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != BDM_OK:
+            msg = load().bdm_mbatch_last_error(h).decode() if h else ""
+            if h:
+                load().bdm_mbatch_destroy(h)
+            raise BdmError(rc, msg)
+        self.h = h
+
+    def _check(self, rc):
+        if rc != BDM_OK:
+            raise BdmError(rc, load().bdm_mbatch_last_error(self.h).decode())
+
+    def load_sim(self, slot, params, x, y, z, diameter, steps):
+        p = make_params(dict(params, kind="mechanics"))
+        x, y, z = (np.ascontiguousarray(a, np.float64) for a in (x, y, z))
+        d = np.ascontiguousarray(diameter, np.float32)
+        self._check(load().bdm_mbatch_load(self.h, int(slot), ctypes.byref(p), len(x), _ptr(x), _ptr(y),
+                                           _ptr(z), _ptr(d), int(steps)))
+
+    def step(self, n=1):
+        self._check(load().bdm_mbatch_step(self.h, int(n)))
+
+    def poll(self):
+        out = np.empty(self.slots, np.int32)
+        self._check(load().bdm_mbatch_poll(self.h, _ptr(out)))
+        return out
+
+    def get_state(self, slot, fields=("x", "y", "z", "diameter", "neighbour_count", "box_id")):
+        L = load()
+        st = State()
+        st.struct_size = ctypes.sizeof(State)
+        self._check(L.bdm_mbatch_get_state(self.h, int(slot), ctypes.byref(st)))
+        n = st.n
+        arrays = {f: np.empty(n, _DTYPES[f]) for f in fields}
+        st2 = State()
+        st2.struct_size = ctypes.sizeof(State)
+        for f, a in arrays.items():
+            setattr(st2, f, a.ctypes.data)
+        self._check(L.bdm_mbatch_get_state(self.h, int(slot), ctypes.byref(st2)))
+        res = dict(arrays)
+        res.update(n=int(st2.n), step=int(st2.step), grid_origin_q=np.array(st2.grid_origin_q[:], np.int64),
+                   grid_box_q=int(st2.grid_box_q), grid_dims=np.array(st2.grid_dims[:], np.int64))
+        return res
+
+    def release(self, slot):
+        self._check(load().bdm_mbatch_release(self.h, int(slot)))
+
+    def close(self):
+        if self.h:
+            load().bdm_mbatch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

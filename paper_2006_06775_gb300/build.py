@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbdm.so")
-SOURCES = ["grid.cu", "mechanics.cu", "diffusion.cu", "sir.cu", "batch.cu", "noalloc.cu", "neurite.cu",
+SOURCES = ["grid.cu", "mechanics.cu", "diffusion.cu", "sir.cu", "batch.cu", "mbatch.cu", "noalloc.cu", "neurite.cu",
            "api.cu"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

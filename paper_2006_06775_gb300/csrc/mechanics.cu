@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "mechcore.cuh"
 
 namespace bdm {
 
@@ -150,30 +151,6 @@ constexpr int kCL = 16;    // candidate list length per thread
 constexpr int kBQ = 8;     // band queue length per thread
 constexpr unsigned kDenseBox = 8;  // agents per box above which a row run is treated as dense
 
-__device__ __forceinline__ void contact_force(float& Fx, float& Fy, float& Fz, float ex, float ey,
-                                              float ez, float ri, float rj, float kf, float gf) {
-  const float d2 = ex * ex + ey * ey + ez * ez;
-  const float rs = ri + rj;
-  const float rinv = rsqrtf(d2);
-  const float delta = rs - d2 * rinv;
-  if (delta > 0.f) {
-    const float rd = __fdividef(ri * rj, rs) * delta;  // rho * delta > 0
-    const float F = kf * delta - gf * (rd * rsqrtf(rd));
-    const float sc = F * rinv;
-    Fx += sc * ex;
-    Fy += sc * ey;
-    Fz += sc * ez;
-  }
-}
-
-__device__ __forceinline__ unsigned fp64_within(unsigned i, unsigned j, const double* __restrict__ sx,
-                                                 const double* __restrict__ sy,
-                                                 const double* __restrict__ sz, double R2) {
-  const double ax = __dsub_rn(sx[i], sx[j]), ay = __dsub_rn(sy[i], sy[j]), az = __dsub_rn(sz[i], sz[j]);
-  const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
-  return e2 < R2 ? 1u : 0u;
-}
-
 // FP64 decision of one band candidate, as a real call: a conditional call inside a loop cannot be
 // if-converted, so the loop never occupies GB300's slow FP64 pipe for candidates outside the band.
 __device__ __noinline__ unsigned fp64_within_call(unsigned i, unsigned j, const double* __restrict__ sx,
@@ -203,7 +180,7 @@ __device__ __noinline__ unsigned band_rescan(
       const float4 q = p4[j];
       const float px = pi.x - (j < m1 ? -Lf : (j < m2 ? 0.f : Lf));
       const float ex = px - q.x, ey = py - q.y, ez = pz - q.z;
-      const float dd = ex * ex + ey * ey + ez * ez;
+      const float dd = pair_d2(ex, ey, ez);
       if (dd < R2lo) ++k;
       else if (dd <= R2hi) k += fp64_within_call(i, j, sx, sy, sz, R2);
     }
@@ -257,7 +234,7 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
         const float ex = (pi.x + sh.x) - q.x;
         const float ey = (pi.y + sh.y) - q.y;
         const float ez = (pi.z + sh.z) - q.z;
-        const float dd = ex * ex + ey * ey + ez * ez;
+        const float dd = pair_d2(ex, ey, ez);
         if (dd < R2lo) {
           ++cnt;
         } else {  // near R: queued for the FP64 decision after the loop
@@ -286,7 +263,7 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
           const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
           const float ey = py - q.y;
           const float ez = pz - q.z;
-          const float dd = ex * ex + ey * ey + ez * ez;
+          const float dd = pair_d2(ex, ey, ez);
           s_cj[nc][t] = j;  // kept only if within R (every neighbour, band candidate and contact)
           s_cc[nc][t] = (unsigned char)(sg * 3 + (int)bx);
           nc += dd <= R2hi ? 1 : 0;
@@ -309,12 +286,8 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
       for (unsigned k = 0; k < nband; ++k) cnt += fp64_within(i, s_bq[k][t], sx, sy, sz, R2);
     }
     cnt -= 1u;  // the agent itself
-    float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
-    const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
-    if (n2 > c.capf * c.capf) {
-      const float f = c.capf * rsqrtf(n2);
-      Dx *= f; Dy *= f; Dz *= f;
-    }
+    float Dx, Dy, Dz;
+    capped_displacement(Fx, Fy, Fz, c.dtf, c.capf, Dx, Dy, Dz);
     const double nx = __dadd_rn(xi, f2d_exact(Dx));
     const double ny = __dadd_rn(yi, f2d_exact(Dy));
     const double nz = __dadd_rn(zi, f2d_exact(Dz));
@@ -368,7 +341,7 @@ __device__ __noinline__ unsigned list_rescan(unsigned i, unsigned m, const unsig
     const float ex = (pi.x - (float)(bxk - 1) * Lf) - q.x;
     const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
     const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
-    const float dd = ex * ex + ey * ey + ez * ez;
+    const float dd = pair_d2(ex, ey, ez);
     if (dd < R2lo) ++k;
     else if (dd <= R2hi) k += fp64_within_call(i, j, sx, sy, sz, R2);
   }
@@ -522,7 +495,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
         const float ex = (bxk == 0 ? pxm : (bxk == 1 ? px0 : pxp)) - q.x;
         const float ey = pi.y - (float)(sgk % 3 - 1) * Lf - q.y;
         const float ez = pi.z - (float)(sgk / 3 - 1) * Lf - q.z;
-        const float dd = ex * ex + ey * ey + ez * ez;
+        const float dd = pair_d2(ex, ey, ez);
         if (dd < R2lo) {
           ++cnt;
         } else {  // near R: queued for the FP64 decision after the loop
@@ -558,7 +531,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
             const float ex = (bx == 0 ? pxm : (bx == 1 ? px0 : pxp)) - q.x;
             const float ey = py - q.y;
             const float ez = pz - q.z;
-            const float dd = ex * ex + ey * ey + ez * ez;
+            const float dd = pair_d2(ex, ey, ez);
             const unsigned code = (unsigned)(sg * 3 + (int)bx);
             if (dd <= L2 && j != i) {  // within R + skin: listed for the steps until the rebuild
               if (ln < kListCap) list[list_at(i, ln)] = (j << 5) | code;
@@ -618,7 +591,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
           const float ex = (pi.x + sh.x) - q[u].x;
           const float ey = (pi.y + sh.y) - q[u].y;
           const float ez = (pi.z + sh.z) - q[u].z;
-          const float dd = ex * ex + ey * ey + ez * ez;
+          const float dd = pair_d2(ex, ey, ez);
           cnt += dd < R2lo ? 1u : 0u;
           if (dd >= R2lo && dd <= R2hi) {  // near R: queued for the FP64 decision after the loop
             if (nband < (unsigned)kBQ) s_bq[nband][t] = v[u] >> 5;
@@ -644,12 +617,8 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
         for (unsigned k = 0; k < nband; ++k) cnt += fp64_within(i, s_bq[k][t], sx, sy, sz, R2);
       }
     }
-    float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
-    const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
-    if (n2 > c.capf * c.capf) {
-      const float f = c.capf * rsqrtf(n2);
-      Dx *= f; Dy *= f; Dz *= f;
-    }
+    float Dx, Dy, Dz;
+    capped_displacement(Fx, Fy, Fz, c.dtf, c.capf, Dx, Dy, Dz);
     if (!still) nbr[i] = cnt;  // a stationary agent keeps the previous step's count
     const bool moved = Dx != 0.f || Dy != 0.f || Dz != 0.f;
     if (mnext) mnext[i] = moved ? 1 : 0;
@@ -804,7 +773,7 @@ __global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p
         const float ex = (pi.x - (float)((int)bx - 1) * Lf) - q.x;
         const float ey = py - q.y;
         const float ez = pz - q.z;
-        const float dd = ex * ex + ey * ey + ez * ez;
+        const float dd = pair_d2(ex, ey, ez);
         if (dd <= L2 && j != i) {
           if (ln < (unsigned)kListCap) list[list_at(i, ln)] = (j << 5) | (cb + bx);
           ++ln;
@@ -1001,7 +970,7 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed_pairs(
             const float ex = fmaf(-((float)bx - 1.f), Lf, po.x) - q.x;
             const float ey = (po.y - shy) - q.y;
             const float ez = (po.z - shz) - q.z;
-            const float dd = ex * ex + ey * ey + ez * ez;
+            const float dd = pair_d2(ex, ey, ez);
             if (dd < R2lo) atomicAdd(&s_cnt[w][o], 1u);
             else if (dd <= R2hi) {
               const unsigned pos = atomicAdd(&s_nb[w], 1u);
@@ -1040,12 +1009,8 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed_pairs(
     __syncwarp();
     if (valid) {
       const double xi = sx[i], yi = sy[i], zi = sz[i];
-      float Dx = c.dtf * Fx, Dy = c.dtf * Fy, Dz = c.dtf * Fz;
-      const float n2 = Dx * Dx + Dy * Dy + Dz * Dz;
-      if (n2 > c.capf * c.capf) {
-        const float f = c.capf * rsqrtf(n2);
-        Dx *= f; Dy *= f; Dz *= f;
-      }
+      float Dx, Dy, Dz;
+      capped_displacement(Fx, Fy, Fz, c.dtf, c.capf, Dx, Dy, Dz);
       const double nx = __dadd_rn(xi, f2d_exact(Dx));
       const double ny = __dadd_rn(yi, f2d_exact(Dy));
       const double nz = __dadd_rn(zi, f2d_exact(Dz));

@@ -167,3 +167,15 @@ def test_create_rejects_unlaunchable_diffusion_grid(lib):
     assert rc == bdm.BDM_EINVAL
     assert b"launch limits" in lib.bdm_last_error(h)
     lib.bdm_destroy(h)
+
+
+@pytest.mark.parametrize("precision,slots,cap", [(7, 4, 100), (bdm.BDM_MIXED, 0, 100),
+                                                  (bdm.BDM_FP64, 4, 0), (bdm.BDM_MIXED, 1 << 16, 1 << 16)])
+def test_mbatch_create_rejects_bad_shapes_before_any_cuda_call(lib, precision, slots, cap):
+    """A bad precision, an empty pool or a pool of 2^31 agent places or more is refused before any
+    stream or device memory is created (this runs without a GPU)."""
+    h = ctypes.c_void_p()
+    rc = lib.bdm_mbatch_create(precision, slots, cap, None, ctypes.byref(h))
+    assert rc == bdm.BDM_EINVAL
+    assert b"below 2^31" in lib.bdm_mbatch_last_error(h)
+    lib.bdm_mbatch_destroy(h)
