@@ -429,6 +429,11 @@ def run_ours(args):
             "neurite": neurite, "ensemble": ensemble,
             "serving": serving,
         }
+        if serving:
+            for key, arm in (("served", "served"), ("no_pool", "served_no_pool"),
+                             ("alone", "one_at_a_time"), ("alone_plain", "one_at_a_time_plain")):
+                line["serve_%s_sims_per_s" % key] = serving[arm]["sims_per_s"]
+                line["serve_%s_p99_s" % key] = serving[arm]["p99_s"]
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -701,24 +706,47 @@ def bench_spheroid(max_agents=1_000_000, max_steps=160):
 
 def bench_serving(count):
     """Served request stream (Poisson 200/s, sizes log-uniform 1e3..1e6, 50..500 steps, 70%
-    mechanics / 30% SIR, 150 GB budget) against the same trace one simulation at a time."""
+    mechanics / 30% SIR, 150 GB budget).  Arms on the same trace:
+      served            mechanics up to 32,768 agents in a 64-slot pool (one launch sequence per
+                        step for all of them), larger ones and SIR on own handles over 16 streams,
+                        mechanics handles with 2.5 um neighbour lists
+      served_no_pool    the same without the pool (every request on its own handle)
+      one_at_a_time     FIFO, one simulation at a time, mechanics with the same 2.5 um lists
+      one_at_a_time_plain   the same with the plain kernels (grid rebuilt every step)"""
     from paper_2006_06775_gb300 import serve
     reqs = synth.request_stream(count=count)
     payloads = {r.rid: serve.payload(r) for r in reqs}
     warm = [synth.Request(10 ** 6 + k, 0.0, kind, 2000, 10, 7 + k) for k, kind in
-            enumerate(("mechanics", "sir"))]
+            enumerate(("mechanics", "sir", "mechanics"))]
+    warm[2] = synth.Request(10 ** 6 + 2, 0.0, "mechanics", 200_000, 10, 9)
     wp = {r.rid: serve.payload(r) for r in warm}
     serve.run_one_at_a_time(serve.GpuExecutor(1), warm, lambda r: wp[r.rid])
-    # served: neighbour lists (the tuned 2.5 um skin) for mechanics, 16 streams; the baseline runs
-    # the same trace one simulation at a time with the plain kernels (grid rebuilt every step)
-    served = serve.Server(serve.GpuExecutor(streams=16, mechanics_skin=2.5), budget_bytes=150e9,
-                          max_active=64, chunk=25).run(reqs, lambda r: payloads[r.rid])
-    alone = serve.run_one_at_a_time(serve.GpuExecutor(streams=1), reqs, lambda r: payloads[r.rid])
-    out = serve.summarize(served)
+    serve.run_one_at_a_time(serve.GpuExecutor(1, mechanics_skin=2.5), warm, lambda r: wp[r.rid])
+    pool_slots, pool_cap, chunk = 64, 32768, 25
+
+    def served_arm(pool):
+        ex = serve.GpuExecutor(streams=16, mechanics_skin=2.5, pool_slots=pool_slots if pool else 0,
+                               pool_capacity=pool_cap, pool_chunk=chunk)
+        if pool:
+            ex.warm_pool(wp[warm[0].rid], 2 * chunk)
+        jobs = serve.Server(ex, budget_bytes=150e9, max_active=64, chunk=chunk).run(
+            reqs, lambda r: payloads[r.rid])
+        ex.shutdown()
+        return jobs
+
+    served = served_arm(True)
+    out = {"trace": "all %d requests of the Poisson stream (seed 4)" % count,
+           "served": serve.summarize(served)}
+    out["served"]["pooled_requests"] = sum(j.pooled for j in served)
+    out["served"]["pool"] = {"slots": pool_slots, "slot_capacity": pool_cap, "chunk_steps": chunk,
+                             "launches_per_step": 9}
+    out["served_no_pool"] = serve.summarize(served_arm(False))
+    out["one_at_a_time"] = serve.summarize(serve.run_one_at_a_time(
+        serve.GpuExecutor(streams=1, mechanics_skin=2.5), reqs, lambda r: payloads[r.rid]))
+    out["one_at_a_time_plain"] = serve.summarize(serve.run_one_at_a_time(
+        serve.GpuExecutor(streams=1), reqs, lambda r: payloads[r.rid]))
     out["mechanics_skin_um"] = 2.5
     out["streams"] = 16
-    out["one_at_a_time"] = serve.summarize(alone)
-    out["trace"] = "first %d requests of the Poisson stream (seed 4)" % count
     return out
 
 
@@ -776,7 +804,7 @@ def main():
                     help="skip the plain-mechanics and tumour-spheroid sub-benchmarks")
     ap.add_argument("--ensemble-steps", type=int, default=1000)
     ap.add_argument("--ensemble-baseline-runs", type=int, default=16)
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--neurite-agents", type=int, default=9_000_000,
                     help="agents of the neuron-forest sub-benchmark (0: skip it)")
     ap.add_argument("--neurite-only", action="store_true",
