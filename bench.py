@@ -625,8 +625,10 @@ def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_ste
 
 def bench_stationary(n=10_000_000, steps=10, warmup=3, skin=2.5):
     """A settled lattice around a relaxing ball (10% of 10^7 agents), neighbour lists with a 2.5 um
-    skin: steps with stationary agents skipped against the same steps evaluating every agent (the
-    results are identical).  `skipped_per_list_step` is the fraction of agents skipped on a list step."""
+    skin: steps with stationary warps skipped against the same steps evaluating every agent (the
+    results are identical).  `skipped_per_list_step` is the fraction of agents skipped on a list
+    step; `list_kernel_ms_per_list_step` times the list kernel (with the skip, plus the kernel that
+    picks the warps) on list steps alone, from a separately profiled run."""
     from paper_2006_06775_gb300 import bdm
     params, inp = synth.settled_mechanics(n, 0.1)
     R = float(np.max(inp["diameter"]))
@@ -641,13 +643,30 @@ def bench_stationary(n=10_000_000, steps=10, warmup=3, skin=2.5):
         s0 = sim.get_state(fields=())
         ms = _event_time_ms(sim.stream, lambda: sim.step(steps))
         s1 = sim.get_state(fields=())
+        # the list kernel on list steps alone (events around each kernel, one step at a time)
+        sim.profile(True)
+        prev, list_ms, list_steps = {}, 0.0, 0
+        for _ in range(steps):
+            r0 = int(sim.get_state(fields=())["grid_rebuilds"])
+            sim.step(1)
+            r1 = int(sim.get_state(fields=())["grid_rebuilds"])
+            cur = {k: v[1] for k, v in sim.kernel_times().items()}
+            d = {k: cur[k] - prev.get(k, 0.0) for k in cur}
+            prev = cur
+            if r1 == r0:
+                list_ms += d.get("force_list", 0.0) + d.get("still_warps", 0.0)
+                list_steps += 1
+        sim.profile(False)
         sim.close()
         rebuilds = int(s1["grid_rebuilds"]) - int(s0["grid_rebuilds"])
         skipped = int(s1["stationary_skipped"]) - int(s0["stationary_skipped"])
         out[key] = {"ms_per_step": ms / steps, "agent_steps_per_s": n * steps / (ms * 1e-3),
                     "grid_rebuilds": rebuilds,
-                    "skipped_per_list_step": skipped / max(1, n * (steps - rebuilds))}
+                    "skipped_per_list_step": skipped / max(1, n * (steps - rebuilds)),
+                    "list_kernel_ms_per_list_step": list_ms / max(1, list_steps)}
     out["speedup"] = out["evaluate_all"]["ms_per_step"] / out["skip"]["ms_per_step"]
+    out["list_step_kernel_speedup"] = (out["evaluate_all"]["list_kernel_ms_per_list_step"] /
+                                       out["skip"]["list_kernel_ms_per_list_step"])
     return out
 
 

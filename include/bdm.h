@@ -108,10 +108,11 @@ typedef struct bdm_params {
   uint64_t capacity;             /* max agents (growth appends up to it); 0 = agents of the first
                                     bdm_add_agents call                                           */
   uint64_t box_capacity;         /* max grid boxes; 0 = automatic (4 x initial + margin)           */
-  /* Stationary agents (skin > 0): on a list step an agent that, with every listed neighbour, kept
-     its position in the previous step would get the same force, displacement (zero) and neighbour
-     count again, so it can be left out.  The results are identical either way. */
-  int32_t skip_stationary;       /* 1 = skip such agents; 0 = evaluate every agent every step     */
+  /* Stationary agents (skin > 0): on a list step a warp-sized group of agents (32 consecutive in
+     the sorted order) whose agents, and every agent in the boxes around them, kept their positions
+     in the previous step would get the same forces, displacements (zero) and neighbour counts
+     again, so it is left out.  The results are identical either way. */
+  int32_t skip_stationary;       /* 1 = skip such groups; 0 = evaluate every agent every step     */
   int32_t reserved4;
   /* Oncology behaviours (readings R13, R14; the grid is then rebuilt every step, skin = 0). */
   double brownian_sigma;         /* Brownian migration: after the capped mechanical update every

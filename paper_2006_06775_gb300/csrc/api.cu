@@ -381,10 +381,11 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
           (rc = dalloc_n(s, &b.p4set[1], C)))
         return rc;
       const size_t ngrp = (C + 31) / 32;
-      if (p.skip_stationary && ((rc = dalloc_n(s, &b.moved[0], C)) || (rc = dalloc_n(s, &b.moved[1], C)) ||
-                                (rc = dalloc_n(s, &b.wmoved[0], ngrp)) || (rc = dalloc_n(s, &b.wmoved[1], ngrp)) ||
-                                (rc = dalloc_n(s, &b.wbounds, ngrp))))
+      if (p.skip_stationary && ((rc = dalloc_n(s, &b.wmoved[0], ngrp)) || (rc = dalloc_n(s, &b.wmoved[1], ngrp)) ||
+                                (rc = dalloc_n(s, &b.wbounds, ngrp)) || (rc = dalloc_n(s, &b.wrows, 9 * ngrp)) ||
+                                (rc = dalloc_n(s, &b.evl, ngrp))))
         return rc;
+      b.wstride = ngrp;
       CK(cudaMemsetAsync(b.list_n, 0, sizeof(unsigned) * C, s->stream));
       CK(cudaMemsetAsync(b.disp, 0, sizeof(float) * C, s->stream));
     }
@@ -545,6 +546,7 @@ int enqueue_mech_step(bdm_sim* s) {
     RUN("attr_copy", 1, launch_attr_copy(st, B, A, g, s->blocks_stream));
     RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_list));
     RUN("force_walk", 1, launch_force_skin(st, b, s->pos_cur, g, s->mc, true, s->blocks_walk));  // overflow only
+    if (s->mc.skip_stationary) RUN("still_warps", 1, launch_still_warps(st, b, s->pos_cur, g, s->blocks_stream));
     RUN("force_list", 1, launch_force_skin(st, b, s->pos_cur, g, s->mc, false, s->blocks_force));
     s->pos_cur ^= 1;  // the force kernels wrote the step's result into the other position set
     point_current(s);

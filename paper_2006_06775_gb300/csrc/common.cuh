@@ -71,6 +71,8 @@ struct DevGrid {
   float Lf_list;                  // box length (um) of the grid the lists were built on
   unsigned n_step;                // agents the last step moved (a list step's box-id read-out)
   unsigned long long skipped;     // agent evaluations skipped as stationary (list steps)
+  unsigned n_eval;                // stationary skip: warps listed for evaluation this step
+  unsigned reserved_eval;
 };
 
 struct MechConsts {               // per-simulation constants passed by value
@@ -272,11 +274,16 @@ struct MechBuffers {
   unsigned* list;
   unsigned* list_n;
   float* disp;                   // |moves| of each agent since the last rebuild
-  unsigned char* moved[2];       // 1 if the agent's displacement was nonzero (alternate like pset)
-  // stationary skip: 1 if any agent of a warp-sized group moved (alternate like pset), and each
-  // group's bounds, largest diameter and move since the rebuild as of its last evaluation
-  unsigned char* wmoved[2];
+  // stationary skip, per warp-sized group of agents (32 consecutive in the sorted order): a bit per
+  // agent, set if it moved (alternate like pset); its bounds, largest diameter and move since the
+  // rebuild as of its last evaluation; and, from the last rebuild, for each of the nine neighbour
+  // rows two ranges [first, end) of agents holding every candidate of its agents (row-major: row
+  // sg of group w at sg * wstride + w)
+  unsigned* wmoved[2];
   struct WarpBounds* wbounds;
+  uint4* wrows;
+  size_t wstride;
+  unsigned* evl;                 // warps listed for evaluation on a list step
 };
 
 // grid.cu
@@ -302,6 +309,7 @@ constexpr unsigned kListCap = 32;  // listed candidates per agent (R + skin)
 void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g, MechConsts c,
                        bool build, int grid_blocks);
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
+void launch_still_warps(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g, int grid_blocks);
 void launch_attr_copy(cudaStream_t s, const AgentArrays& src, const AgentArrays& dst, DevGrid* g,
                       int grid_blocks);
 int force_skin_blocks_per_sm(bool build);

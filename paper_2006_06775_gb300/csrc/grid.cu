@@ -37,6 +37,7 @@ __global__ void k_finalize(DevGrid* g, MechConsts c) {
   const unsigned n = g->n;
   g->scan_ctr[0] = 0;
   g->scan_ctr[1] = 0;
+  g->n_eval = 0;
   grid_from_bounds(g, c);
   // Rebuild the grid this step, or evaluate the neighbour lists of the last rebuild (skin > 0).  A
   // pair within R now was within R + skin at the last rebuild while no agent has moved more than

@@ -150,6 +150,7 @@ constexpr int kFT = 256;   // threads per CTA
 constexpr int kCL = 16;    // candidate list length per thread
 constexpr int kBQ = 8;     // band queue length per thread
 constexpr unsigned kDenseBox = 8;  // agents per box above which a row run is treated as dense
+constexpr unsigned kSkipSpan = 16;  // stationary skip: a row range over more warps is evaluated
 
 // FP64 decision of one band candidate, as a real call: a conditional call inside a loop cannot be
 // if-converted, so the loop never occupies GB300's slow FP64 pipe for candidates outside the band.
@@ -360,9 +361,10 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     const float4* __restrict__ p4, double* __restrict__ ox, double* __restrict__ oy,
     double* __restrict__ oz, float4* __restrict__ op4, unsigned* __restrict__ skey,
     const unsigned* __restrict__ start, unsigned* __restrict__ list, unsigned* __restrict__ list_n,
-    float* __restrict__ disp, unsigned* __restrict__ nbr, const unsigned char* __restrict__ mprev,
-    unsigned char* __restrict__ mnext, const unsigned char* __restrict__ wprev,
-    unsigned char* __restrict__ wnext, WarpBounds* __restrict__ wcache, DevGrid* g, MechConsts c) {
+    float* __restrict__ disp, unsigned* __restrict__ nbr,
+    unsigned* __restrict__ wnext, WarpBounds* __restrict__ wcache,
+    const unsigned* __restrict__ evl, double* __restrict__ rx, double* __restrict__ ry,
+    double* __restrict__ rz, DevGrid* g, MechConsts c) {
   // BUILD: the walk with forces, only on a rebuild step whose lists overflowed; otherwise the lists
   // (built by k_list_build on a rebuild step) give the forces
   if (BUILD ? !(g->rebuild && g->list_overflow) : g->list_overflow != 0u) return;
@@ -374,7 +376,6 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   __shared__ unsigned long long s_mn[3][kFT], s_mx[3][kFT];
   __shared__ unsigned s_md[kFT];
   __shared__ float s_dm[kFT];
-  __shared__ unsigned s_skip;  // agents of the block skipped as stationary
   // list steps: the next agent's offsets, list length and first four entries are copied ahead
   // (double-buffered), and this agent's FP64 centre and move arrive during its force loop
   __shared__ float4 s_pi[2][kFT];
@@ -405,7 +406,6 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   }
   s_md[t] = 0u;
   s_dm[t] = 0.f;
-  if (t == 0) s_skip = 0u;
   __syncthreads();
   const unsigned stride = gridDim.x * blockDim.x;
   auto prefetch = [&](unsigned a, int b) {  // list step: agent a's offsets, list length, entries 0-3
@@ -414,62 +414,35 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
 #pragma unroll
     for (int u = 0; u < 4; ++u) cp_async_n<4>(&s_v[b][u][t], list + list_at(a, (unsigned)u));
   };
-  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   int buf = 0;
-  // stationary agents are looked for only from the second list step after a rebuild: a rebuild
-  // renumbers the agents, and it writes only one of the two position sets, so the other holds the
-  // agents' centres again only once the first list step has written it
-  const bool look = SKIP && !BUILD && !rb && g->since_rebuild >= 2u;
+  // The agents this launch evaluates: every agent, or with the stationary skip the warps (32
+  // consecutive agents) that k_still_warps listed.  There a lane past the last agent repeats the
+  // last agent, so the warp stays whole and writes the same values twice.
+  const unsigned lane = (unsigned)t & 31u;
+  unsigned k = SKIP ? (blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned kstep = SKIP ? stride >> 5 : stride;
+  const unsigned kend = SKIP ? (n ? g->n_eval : 0u) : n;
+  auto agent = [&](unsigned w) -> unsigned {
+    const unsigned a = w * 32u + lane;
+    return a < n ? a : n - 1u;
+  };
+  // listed warps of this and the next iteration (loaded one iteration ahead of their use)
+  unsigned wcur = 0, wnxt = 0, wnn = 0;
+  if constexpr (SKIP) {
+    if (k < kend) wcur = __ldg(evl + k);
+    if (k + kstep < kend) wnxt = __ldg(evl + k + kstep);
+  }
   if constexpr (!BUILD) {
-    if (i < n) prefetch(i, 0);
+    if (k < kend) prefetch(SKIP ? agent(wcur) : k, 0);
     cp_async_commit();
   }
-  for (; i < n; i += stride) {
+  for (; k < kend; k += kstep, wcur = wnxt, wnxt = wnn) {
+    const unsigned i = SKIP ? agent(wcur) : k;
+    if constexpr (SKIP) wnn = k + 2u * kstep < kend ? __ldg(evl + k + 2u * kstep) : 0u;
     float4 pi;
-    bool still = false;
-    const bool own_still = look && __ldg(mprev + i) == 0;
     double x0 = 0.0, y0 = 0.0, z0 = 0.0;  // this agent's step-start centre
     float dprev = 0.f;
-    if constexpr (SKIP && !BUILD) {
-      // stationary: this agent kept its position in the previous step and so did every agent of
-      // the warps its listed neighbours belong to, so its evaluation would repeat (zero
-      // displacement, the same count).  A warp whose agents are all stationary is skipped whole:
-      // both position sets already hold its centres and offsets (they did not move), so nothing is
-      // rewritten, and its bounds come from the warp's cache.
-      if (i + stride < n) prefetch(i + stride, buf ^ 1);
-      cp_async_commit();
-      cp_async_wait<1>();  // this agent's prefetch (issued one iteration earlier) has landed
-      pi = s_pi[buf][t];
-      if (own_still) {
-        const unsigned ml = s_m[buf][t];
-        still = true;
-        for (unsigned k = 0; k < ml && still; ++k) {
-          const unsigned v = k < 4u ? s_v[buf][k][t] : __ldg(list + list_at(i, k));
-          still = __ldg(wprev + (v >> 10)) == 0;  // the warp of agent v >> 5
-        }
-      }
-      const unsigned am = __activemask();
-      if (look && __all_sync(am, still)) {
-        mnext[i] = 0;
-        if ((t & 31) == 0) {
-          const WarpBounds wb = wcache[i >> 5];
-          wnext[i >> 5] = 0;
-          for (int a = 0; a < 3; ++a) {
-            s_mn[a][t] = wb.mn[a] < s_mn[a][t] ? wb.mn[a] : s_mn[a][t];
-            s_mx[a][t] = wb.mx[a] > s_mx[a][t] ? wb.mx[a] : s_mx[a][t];
-          }
-          s_md[t] = wb.md > s_md[t] ? wb.md : s_md[t];
-          s_dm[t] = fmaxf(s_dm[t], wb.dm);
-          atomicAdd(&s_skip, (unsigned)__popc(am));
-        }
-        buf ^= 1;
-        continue;
-      }
-      x0 = sx[i];  // evaluated: centre and move requested now, used after the force loop
-      y0 = sy[i];
-      z0 = sz[i];
-      dprev = disp[i];
-    } else if constexpr (BUILD) {
+    if constexpr (BUILD) {
       pi = __ldg(p4 + i);
     } else {
       cp_async_n<8>(&s_c[0][t], sx + i);
@@ -477,7 +450,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
       cp_async_n<8>(&s_c[2][t], sz + i);
       cp_async_n<4>(&s_d[t], disp + i);
       cp_async_commit();
-      if (i + stride < n) prefetch(i + stride, buf ^ 1);
+      if (k + kstep < kend) prefetch(SKIP ? agent(wnxt) : i + stride, buf ^ 1);
       cp_async_commit();
       cp_async_wait<2>();  // this agent's prefetch (issued one iteration earlier) has landed
       pi = s_pi[buf][t];
@@ -562,9 +535,7 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     } else {
       // four entries at a time, their loads and their candidates' loads issued together, so the loop
       // does not wait on one dependent load pair per entry
-      // stationary: this agent and every listed neighbour kept their position in the previous step,
-      // so the evaluation would repeat (zero displacement, the same count): it is skipped
-      const unsigned m = still ? 0u : s_m[buf][t];
+      const unsigned m = s_m[buf][t];
       // the warp runs to its longest list (a uniform bound: no lane leaves the loop early; slots
       // past a lane's list are evaluated as far away and add nothing)
       const unsigned mw = __reduce_max_sync(__activemask(), m);  // lanes past n have left the loop
@@ -619,9 +590,8 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     }
     float Dx, Dy, Dz;
     capped_displacement(Fx, Fy, Fz, c.dtf, c.capf, Dx, Dy, Dz);
-    if (!still) nbr[i] = cnt;  // a stationary agent keeps the previous step's count
+    nbr[i] = cnt;
     const bool moved = Dx != 0.f || Dy != 0.f || Dz != 0.f;
-    if (mnext) mnext[i] = moved ? 1 : 0;
     // update: FP64 centre += displacement (exact conversion, one FP64 add), FP32 offset +=
     // displacement, move since the rebuild (a list step's box ids are derived on read-out:
     // k_readout_box)
@@ -629,8 +599,6 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
       x0 = sx[i];
       y0 = sy[i];
       z0 = sz[i];
-    } else if constexpr (SKIP) {
-      buf ^= 1;
     } else {
       cp_async_wait<1>();  // this agent's centre and move (the newest group is the next prefetch)
       x0 = s_c[0][t];
@@ -645,6 +613,16 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     ox[i] = nx;
     oy[i] = ny;
     oz[i] = nz;
+    if constexpr (SKIP && !BUILD) {
+      // a rebuild step's centres go into both position sets (the current one was consumed by the
+      // gather), so on the next step a stationary warp needs no copy: its offsets did not change
+      // either (an unmoved agent's offset plus a zero displacement is the same value)
+      if (rb) {
+        rx[i] = nx;
+        ry[i] = ny;
+        rz[i] = nz;
+      }
+    }
     op4[i] = make_float4(pi.x + Dx, pi.y + Dy, pi.z + Dz, pi.w);
     const float D = (rb ? 0.f : dprev) + sqrtf(Dx * Dx + Dy * Dy + Dz * Dz);
     disp[i] = D;
@@ -661,40 +639,26 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     if constexpr (SKIP && !BUILD) {
       // the warp's cache: bounds of its new centres, its largest diameter and move (lanes past n
       // have left the loop; the active lanes are a prefix of the warp)
-      const unsigned am = __activemask();
-      const int lane = t & 31, na = __popc(am);
-      unsigned long long wmn[3] = {e0, e1, e2}, wmx[3] = {e0, e1, e2};
-      unsigned wmd = dbits;
-      float wdm = D;
+      // (the warp is whole: a lane past the last agent repeats the last agent)
+      const unsigned am = 0xFFFFFFFFu;
+      const unsigned ee[3] = {(unsigned)(e0 >> 32), (unsigned)(e1 >> 32), (unsigned)(e2 >> 32)};
+      const unsigned el[3] = {(unsigned)e0, (unsigned)e1, (unsigned)e2};
+      WarpBounds wb;
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        const bool in = lane + o < na;
-        for (int a = 0; a < 3; ++a) {
-          const unsigned long long u = __shfl_down_sync(am, wmn[a], o);
-          const unsigned long long v = __shfl_down_sync(am, wmx[a], o);
-          if (in) {
-            wmn[a] = u < wmn[a] ? u : wmn[a];
-            wmx[a] = v > wmx[a] ? v : wmx[a];
-          }
-        }
-        const unsigned ud = __shfl_down_sync(am, wmd, o);
-        const float ug = __shfl_down_sync(am, wdm, o);
-        if (in) {
-          wmd = ud > wmd ? ud : wmd;
-          wdm = fmaxf(wdm, ug);
-        }
+      for (int a = 0; a < 3; ++a) {  // 64-bit min / max from two 32-bit warp reductions each
+        const unsigned hn = __reduce_min_sync(am, ee[a]), hx = __reduce_max_sync(am, ee[a]);
+        const unsigned ln = __reduce_min_sync(am, ee[a] == hn ? el[a] : ~0u);
+        const unsigned lx = __reduce_max_sync(am, ee[a] == hx ? el[a] : 0u);
+        wb.mn[a] = ((unsigned long long)hn << 32) | ln;
+        wb.mx[a] = ((unsigned long long)hx << 32) | lx;
       }
+      wb.md = __reduce_max_sync(am, dbits);
+      wb.dm = __uint_as_float(__reduce_max_sync(am, __float_as_uint(D)));  // D >= 0
       const unsigned anymoved = __ballot_sync(am, moved);
-      if (lane == 0) {
-        WarpBounds wb;
-        for (int a = 0; a < 3; ++a) {
-          wb.mn[a] = wmn[a];
-          wb.mx[a] = wmx[a];
-        }
-        wb.md = wmd;
-        wb.dm = wdm;
+      if ((t & 31) == 0) {
         wcache[i >> 5] = wb;
-        wnext[i >> 5] = anymoved ? 1 : 0;
+        wnext[i >> 5] = anymoved;  // lane l: agent 32 (i >> 5) + l (a repeated last agent adds
+                                   // its own bit again or a bit past the last agent, never read)
       }
     }
   }
@@ -710,9 +674,6 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   unsigned long long mx[3] = {s_mx[0][t], s_mx[1][t], s_mx[2][t]};
   block_commit_bounds<kFT>(mn, mx, s_md[t], g);  // contains a __syncthreads
   if (t == 0 && s_dmax) atomicMax(&g->max_disp, s_dmax);
-  if constexpr (SKIP && !BUILD) {  // s_skip is final: block_commit_bounds has synchronised the block
-    if (t == 0 && s_skip) atomicAdd(&g->skipped, (unsigned long long)s_skip);
-  }
 }
 
 // Lists of a rebuild step: the canonical 27-box walk on a grid of box length >= R + skin, keeping
@@ -795,6 +756,148 @@ __global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p
   if (overflow) g->list_overflow = 1u;  // this step's forces come from the walk, the next rebuilds
   listed = warp_reduce(listed, [](unsigned a, unsigned b) { return a + b; });
   if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g->list_entries, (unsigned long long)listed);
+}
+
+// Stationary skip, before the list kernel of every step: which warps (32 consecutive agents in the
+// sorted order) the list kernel evaluates.  On a list step a warp is left out when its agents and
+// every agent of its row ranges kept their positions in the previous step (no moved bit set): its
+// agents' force inputs are those of the previous step, so their evaluation would repeat it (zero
+// displacement, the same counts).  Nothing of a left-out warp is rewritten: both position sets
+// hold its centres and offsets (a rebuild step writes its centres into both), its counts stay, its
+// bounds come from its cache, and its moved bits are cleared.  A rebuild renumbers the agents, so a
+// rebuild step lists every warp and records the row ranges of the new order.  Box keys grow along
+// a warp; for the neighbour row at (dy, dz) the warp's agents in the first agent's row of boxes
+// have their candidates between the first agent's box shifted by (-1, dy, dz) and the end of that
+// row shifted by (dy, dz), and those in the last agent's row between that row's start shifted and
+// the last agent's box shifted by (+1, dy, dz); a warp spanning more rows gets one range from first
+// to last.  Clamping at the grid's faces only widens a range.  One thread per warp; the listed
+// warps are appended in block order (their order enters no result).
+constexpr int kStillT = 256;
+__device__ __forceinline__ uint2 row_range(const unsigned* __restrict__ start, long long ka,
+                                           long long ke, long long nbox) {
+  ka = min(max(ka, 0ll), nbox);
+  ke = min(max(ke, 0ll), nbox);
+  return make_uint2(__ldg(start + ka), __ldg(start + ke));
+}
+
+__global__ void __launch_bounds__(kStillT) k_still_warps(
+    const unsigned* __restrict__ skey, const unsigned* __restrict__ start, uint4* __restrict__ wrows,
+    size_t ws, const unsigned* __restrict__ wprev, unsigned* __restrict__ wnext,
+    const WarpBounds* __restrict__ wcache, unsigned* __restrict__ evl, DevGrid* g) {
+  if (g->list_overflow) return;  // this step's forces come from the walk
+  const unsigned n = g->nbox ? g->n : 0u;
+  const unsigned nw = (n + 31u) / 32u;
+  const bool rb = g->rebuild != 0u;
+  const long long nbox = (long long)g->nbox, d0 = g->dims[0], d1 = g->dims[1];
+  __shared__ unsigned s_cnt[kStillT / 32];
+  __shared__ unsigned s_base;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  unsigned md = 0u, skipped = 0u;
+  for (unsigned W0 = blockIdx.x * kStillT; W0 < nw; W0 += gridDim.x * kStillT) {  // block-uniform
+    const unsigned W = W0 + (unsigned)t;  // this thread's group; a warp takes 32 consecutive ones
+    const bool live = W < nw;
+    bool ev = live;
+    if (rb) {  // the row ranges of the new order (two per row: the first and last agent's)
+      if (live) {
+        const long long kf = __ldg(skey + W * 32u), kl = __ldg(skey + min(W * 32u + 31u, n - 1u));
+        const long long rf = kf / d0, rl = kl / d0;
+#pragma unroll
+        for (int sg = 0; sg < 9; ++sg) {
+          const long long off = ((long long)(sg / 3 - 1) * d1 + (long long)(sg % 3 - 1)) * d0;
+          uint2 r0, r1 = make_uint2(1u, 0u);
+          if (rl == rf || rl > rf + 1) {
+            r0 = row_range(start, kf + off - 1, kl + off + 2, nbox);
+          } else {
+            r0 = row_range(start, kf + off - 1, (rf + 1) * d0 + off, nbox);
+            r1 = row_range(start, rl * d0 + off, kl + off + 2, nbox);
+          }
+          wrows[sg * ws + W] = make_uint4(r0.x, r0.y, r1.x, r1.y);
+        }
+      }
+    } else {
+      // The warp's 32 groups have their candidates of one row within a window of 64 moved words
+      // (2048 agents) from the lowest of their ranges: loaded once by the warp, each lane tests
+      // the bits of its two ranges (a range over more than three words, or past the window, counts
+      // as moved).  The nine rows' loads are issued together.
+      bool dirty = false;
+      uint4 rr[9];
+#pragma unroll
+      for (int sg = 0; sg < 9; ++sg) rr[sg] = live ? wrows[sg * ws + W] : make_uint4(1u, 0u, 1u, 0u);
+      unsigned wmin[9], M0[9], M1[9];
+#pragma unroll
+      for (int sg = 0; sg < 9; ++sg) {
+        const unsigned lo0 = rr[sg].y > rr[sg].x ? rr[sg].x : ~0u;
+        const unsigned lo1 = rr[sg].w > rr[sg].z ? rr[sg].z : ~0u;
+        wmin[sg] = __reduce_min_sync(0xFFFFFFFFu, min(lo0, lo1)) >> 5;  // 2^27 - 1 if all empty
+      }
+#pragma unroll
+      for (int sg = 0; sg < 9; ++sg) {
+        M0[sg] = wmin[sg] + lane < nw ? __ldg(wprev + wmin[sg] + lane) : 0u;
+        M1[sg] = wmin[sg] + 32u + lane < nw ? __ldg(wprev + wmin[sg] + 32u + lane) : 0u;
+      }
+#pragma unroll
+      for (int sg = 0; sg < 9; ++sg) {
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const unsigned lo = part ? rr[sg].z : rr[sg].x, hi = part ? rr[sg].w : rr[sg].y;
+          const bool has = hi > lo;
+          const unsigned a = has ? (lo >> 5) - wmin[sg] : 0u;
+          const unsigned b = has ? ((hi - 1u) >> 5) - wmin[sg] : 0u;
+          if (has && (b - a > 2u || b >= 64u)) dirty = true;
+#pragma unroll
+          for (unsigned j = 0; j < 3u; ++j) {
+            const unsigned wi = min(a + j, 63u);
+            const unsigned v0 = __shfl_sync(0xFFFFFFFFu, M0[sg], (int)(wi & 31u));
+            const unsigned v1 = __shfl_sync(0xFFFFFFFFu, M1[sg], (int)(wi & 31u));
+            if (has && a + j <= b && b < 64u) {
+              const unsigned base = (wmin[sg] + a + j) * 32u;
+              const unsigned s0 = max(lo, base) - base, s1 = min(hi, base + 32u) - base;
+              const unsigned mask = (s1 >= 32u ? ~0u : (1u << s1) - 1u) & ~((1u << s0) - 1u);
+              if ((wi < 32u ? v0 : v1) & mask) dirty = true;
+            }
+          }
+        }
+      }
+      ev = live && dirty;
+      if (live && !dirty) {
+        wnext[W] = 0u;
+        const WarpBounds wb = wcache[W];
+        for (int a = 0; a < 3; ++a) {
+          mn[a] = wb.mn[a] < mn[a] ? wb.mn[a] : mn[a];
+          mx[a] = wb.mx[a] > mx[a] ? wb.mx[a] : mx[a];
+        }
+        md = wb.md > md ? wb.md : md;
+        skipped += min(32u, n - W * 32u);
+      }
+    }
+    // listed groups in thread order, after those other blocks listed before them
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);
+    if (lane == 0) s_cnt[wid] = (unsigned)__popc(m);
+    __syncthreads();
+    if (t == 0) {
+      unsigned tot = 0;
+      for (int w = 0; w < kStillT / 32; ++w) {
+        const unsigned c = s_cnt[w];
+        s_cnt[w] = tot;
+        tot += c;
+      }
+      s_base = tot ? atomicAdd(&g->n_eval, tot) : 0u;
+    }
+    __syncthreads();
+    if (ev) evl[s_base + s_cnt[wid] + (unsigned)__popc(m & ((1u << lane) - 1u))] = W;
+    __syncthreads();  // s_cnt and s_base are rewritten by the next iteration
+  }
+  // one commit per block (same-address atomics from every warp would queue at L2)
+  __shared__ unsigned s_sk[kStillT / 32];
+  skipped = warp_reduce(skipped, [](unsigned a, unsigned b) { return a + b; });
+  if (lane == 0) s_sk[wid] = skipped;
+  block_commit_bounds<kStillT>(mn, mx, md, g);  // contains a __syncthreads
+  if (t == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < kStillT / 32; ++w) tot += s_sk[w];
+    if (tot) atomicAdd(&g->skipped, tot);
+  }
 }
 
 // Box-id read-out after a list step: the box of each agent's step-start centre on that step's grid
@@ -1350,24 +1453,30 @@ void launch_force_skin(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g
     k_force_skin<true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
                                                    b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
                                                    b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
-                                                   b.moved[cur], b.moved[cur ^ 1], b.wmoved[cur],
-                                                   b.wmoved[cur ^ 1], b.wbounds, g, c);
+                                                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                   g, c);
   else if (c.skip_stationary)
     k_force_skin<false, true><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y,
                                                           P.z, b.p4set[cur], N.x, N.y, N.z,
                                                           b.p4set[cur ^ 1], b.skey, b.start, b.list,
-                                                          b.list_n, b.disp, b.nbr, b.moved[cur],
-                                                          b.moved[cur ^ 1], b.wmoved[cur],
-                                                          b.wmoved[cur ^ 1], b.wbounds, g, c);
+                                                          b.list_n, b.disp, b.nbr, b.wmoved[cur ^ 1],
+                                                          b.wbounds, b.evl, P.x, P.y, P.z, g, c);
   else
     k_force_skin<false><<<grid_blocks, kFT, 0, s>>>(b.sorted.x, b.sorted.y, b.sorted.z, P.x, P.y, P.z,
                                                     b.p4set[cur], N.x, N.y, N.z, b.p4set[cur ^ 1],
                                                     b.skey, b.start, b.list, b.list_n, b.disp, b.nbr,
-                                                    nullptr, nullptr, nullptr, nullptr, nullptr, g, c);
+                                                    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                    g, c);
 }
 
 void launch_list_build(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
   k_list_build<<<grid_blocks, kLB, 0, s>>>(b.p4, b.skey, b.start, b.list, b.list_n, g);
+}
+
+void launch_still_warps(cudaStream_t s, const MechBuffers& b, int cur, DevGrid* g, int grid_blocks) {
+  // a quarter of the streaming grid: fewer blocks, fewer commits; each block's rows overlap
+  k_still_warps<<<grid_blocks / 4 > 0 ? grid_blocks / 4 : 1, kStillT, 0, s>>>(b.skey, b.start, b.wrows, b.wstride, b.wmoved[cur],
+                                                b.wmoved[cur ^ 1], b.wbounds, b.evl, g);
 }
 
 void launch_readout_box(cudaStream_t s, const AgentArrays& start_pos, unsigned* skey, DevGrid* g,

@@ -142,8 +142,10 @@ def test_skin_with_secretion_and_diffusion_conserves_mass():
 
 
 def test_stationary_skip_gives_identical_states():
-    """Skipping stationary agents (an agent that, with every listed neighbour, kept its position last
-    step) leaves every result bit-identical, and it does skip on a settled lattice."""
+    """Skipping stationary warps (32 consecutive agents that, with every agent in the boxes around
+    them, kept their positions last step) leaves every result bit-identical, compared after every
+    single step (rebuild steps, the first list step after each, later list steps), and it does skip
+    on a settled lattice."""
     params, inp = synth.settled_mechanics(60_000, 0.2)
     params = dict(params, interaction_radius=R, box_length=R + 2.5, skin=2.5)
     runs = []
@@ -151,8 +153,8 @@ def test_stationary_skip_gives_identical_states():
         sim = bdm.Sim(dict(params, skip_stationary=skip))
         sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
         states = []
-        for _ in range(5):
-            sim.step(6)
+        for k in range(14):  # single steps first (every kind of step compared), then chunks
+            sim.step(1 if k < 10 else 5)
             states.append(sim.get_state())
         runs.append(states)
         sim.close()
@@ -162,7 +164,7 @@ def test_stationary_skip_gives_identical_states():
     assert runs[1][-1]["stationary_skipped"] == 0
     lattice = 60_000 - inp["n_active"]
     assert runs[0][-1]["stationary_skipped"] > lattice
-    assert runs[0][-1]["grid_rebuilds"] < 30
+    assert 2 <= runs[0][-1]["grid_rebuilds"] < 30  # list steps right after a rebuild are covered
 
 
 def test_stationary_skip_matches_oracle_every_step():
