@@ -82,39 +82,17 @@ __device__ __forceinline__ T clamp01(T v) {
 // t = 1, each with the clamped optimal other parameter), and the first in that order whose distance
 // is within a rounding tolerance of the smallest is taken.  That is reading R18's tie rule for
 // parallel segments, whose minimum is not unique.
+// Edge minimiser c of the parallel case: s = 0, s = 1, t = 0, t = 1 (c = 0 .. 3), each with the
+// clamped optimal other parameter.
 template <typename T>
-struct ParamPair {
-  T s, t;
-};
-
-// The parallel case, out of line (it is rare) with every argument a scalar, so the call passes
-// them in registers and the force kernel's register budget is not spent on it.
-template <typename T>
-__device__ __noinline__ ParamPair<T> closest_parallel(T w0, T w1, T w2, T u0, T u1, T u2, T v0,
-                                                      T v1, T v2, T A, T B, T C, T D, T E) {
-  T cs[4], ct[4], dist[4];
-  cs[0] = T(0); ct[0] = clamp01(E / C);
-  cs[1] = T(1); ct[1] = clamp01((B + E) / C);
-  cs[2] = clamp01(-D / A); ct[2] = T(0);
-  cs[3] = clamp01((B - D) / A); ct[3] = T(1);
-  T dmin = T(0);
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const T d0 = (w0 + cs[c] * u0) - ct[c] * v0;
-    const T d1 = (w1 + cs[c] * u1) - ct[c] * v1;
-    const T d2 = (w2 + cs[c] * u2) - ct[c] * v2;
-    dist[c] = sqrt((d0 * d0 + d1 * d1) + d2 * d2);
-    dmin = c == 0 ? dist[c] : (dist[c] < dmin ? dist[c] : dmin);
+__device__ __forceinline__ void edge_minimiser(int c, T A, T B, T C, T D, T E, T& s, T& t) {
+  if (c < 2) {
+    s = c == 0 ? T(0) : T(1);
+    t = clamp01((c == 0 ? E : B + E) / C);
+  } else {
+    t = c == 2 ? T(0) : T(1);
+    s = clamp01((c == 2 ? -D : B - D) / A);
   }
-  const T tol = (sizeof(T) == 4 ? T(1e-5) : T(1e-12)) *
-                ((sqrt(A) + sqrt(C)) + sqrt((w0 * w0 + w1 * w1) + w2 * w2));
-  int pick = 3;
-#pragma unroll
-  for (int c = 2; c >= 0; --c) pick = dist[c] <= dmin + tol ? c : pick;
-  ParamPair<T> r;
-  r.s = pick == 0 ? cs[0] : (pick == 1 ? cs[1] : (pick == 2 ? cs[2] : cs[3]));
-  r.t = pick == 0 ? ct[0] : (pick == 1 ? ct[1] : (pick == 2 ? ct[2] : ct[3]));
-  return r;
 }
 
 template <typename T>
@@ -145,11 +123,29 @@ __device__ __forceinline__ void closest_params(const T P0[3], const T u[3], cons
       den = A * C - B * B;
     }
     if (!(den > T(1e-12) * (A * C))) {
-      const ParamPair<T> r =
-          closest_parallel<T>(w0, w1, w2, u[0], u[1], u[2], v[0], v[1], v[2], A, B, C, D, E);
-      s = r.s;
-      t = r.t;
-      return;
+      // parallel (rare): the smallest distance over the four edge minimisers, then the first of
+      // them within a rounding tolerance of it (two compact passes, not unrolled, so the force
+      // kernel's registers are not spent on this branch)
+      const T tol = (sizeof(T) == 4 ? T(1e-5) : T(1e-12)) *
+                    ((sqrt(A) + sqrt(C)) + sqrt((w0 * w0 + w1 * w1) + w2 * w2));
+      T dmin = T(0);
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          edge_minimiser<T>(c, A, B, C, D, E, s, t);
+          const T d0 = (w0 + s * u[0]) - t * v[0];
+          const T d1 = (w1 + s * u[1]) - t * v[1];
+          const T d2 = (w2 + s * u[2]) - t * v[2];
+          const T dist = sqrt((d0 * d0 + d1 * d1) + d2 * d2);
+          if (pass == 0) {
+            dmin = c == 0 || dist < dmin ? dist : dmin;
+          } else if (dist <= dmin + tol) {
+            return;  // s, t of the first edge minimiser within the tolerance
+          }
+        }
+      }
+      return;  // not reached: the smallest one is within the tolerance of itself
     }
     s = clamp01((B * E - C * D) / den);
     t = (B * s + E) / C;
