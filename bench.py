@@ -378,7 +378,7 @@ def run_ours(args):
         e2e = run_e2e(sim, inp, n, args.e2e_steps, stream)
 
     sim.close()
-    ensemble = serving = plain = spheroid = stationary = oncology = neurite = None
+    ensemble = serving = plain = spheroid = stationary = oncology = neurite = mech_pool = None
     if rank == 0 and args.neurite_agents > 0:
         neurite = bench_neurite(args.neurite_agents)
     if rank == 0 and not args.no_small:
@@ -386,6 +386,7 @@ def run_ours(args):
         spheroid = bench_spheroid()
         oncology = bench_oncology()
         stationary = bench_stationary()
+        mech_pool = bench_mech_pool()
     if rank == 0 and not args.no_ensemble:
         ensemble = bench_ensemble(args.ensemble_steps, args.ensemble_baseline_runs)
     if rank == 0 and args.serve_requests > 0:
@@ -426,9 +427,12 @@ def run_ours(args):
             "diffusion": diffusion,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "plain": plain, "spheroid": spheroid, "oncology": oncology, "stationary": stationary,
-            "neurite": neurite, "ensemble": ensemble,
+            "neurite": neurite, "ensemble": ensemble, "mech_pool": mech_pool,
             "serving": serving,
         }
+        if mech_pool:
+            line["mech_pool_ms_per_step"] = mech_pool["pool_ms_per_step"]
+            line["mech_pool_alone_ms_per_step"] = mech_pool["alone_ms_per_step"]
         if serving:
             for key, arm in (("served", "served"), ("no_pool", "served_no_pool"),
                              ("alone", "one_at_a_time"), ("alone_plain", "one_at_a_time_plain")):
@@ -493,6 +497,46 @@ def _event_time_ms(stream, fn):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+def bench_mech_pool(slots=64, steps=25, seed0=300):
+    """Batched mechanics: 64 served-size simulations (1e3..32,768 agents, log-uniform like the
+    pooled part of the served stream) advanced together in the slot pool, one graph replay of
+    `steps` steps, against the same simulations stepped one after another on their own handles
+    (one stream, each a `steps`-step graph replay).  Both rebuild the grid every step and give
+    bit-identical states."""
+    import math
+    import torch
+    from paper_2006_06775_gb300 import bdm
+    g = np.random.default_rng(seed0)
+    sizes = np.exp(g.uniform(math.log(1e3), math.log(32768), slots)).astype(np.int64)
+    cases = [synth.served_mechanics(int(n), seed0 + k) for k, n in enumerate(sizes)]
+    stream = torch.cuda.Stream()
+    pool = bdm.MechBatch("mixed", slots=slots, slot_capacity=32768, stream=stream)
+    for sl, (params, inp) in enumerate(cases):
+        pool.load_sim(sl, params, inp["x"], inp["y"], inp["z"], inp["diameter"], 1 << 30)
+    pool.step(steps)
+    ms_pool = _event_time_ms(stream, lambda: pool.step(steps)) / steps
+    pool.close()
+    sims = []
+    for params, inp in cases:
+        sim = bdm.Sim(dict(params, skin=0.0), stream=stream)
+        sim.add_agents(inp["x"], inp["y"], inp["z"], inp["diameter"])
+        sim.step(steps)
+        sims.append(sim)
+
+    def alone():
+        for sim in sims:
+            sim.step(steps)
+    ms_alone = _event_time_ms(stream, alone) / steps
+    for sim in sims:
+        sim.close()
+    agents = int(sizes.sum())
+    return {"simulations": slots, "agents": agents, "steps": steps,
+            "pool_ms_per_step": ms_pool, "alone_ms_per_step": ms_alone,
+            "pool_agent_steps_per_s": agents / (ms_pool * 1e-3),
+            "alone_agent_steps_per_s": agents / (ms_alone * 1e-3),
+            "speedup": ms_alone / ms_pool, "pool_launches_per_step": 9}
 
 
 def bench_plain(steps=10, reps=50):
