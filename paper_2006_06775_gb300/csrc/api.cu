@@ -96,6 +96,8 @@ struct bdm_sim {
   std::string err;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t copy_stream = nullptr;          // read-out: host copies beside the permutation
+  cudaEvent_t axis_done[3] = {nullptr, nullptr, nullptr};
   bool poisoned = false;
   bool allocated = false;
   int sms = 152;
@@ -899,16 +901,33 @@ int bdm_get_state(bdm_sim* s, bdm_state* st) {
     const bool pos = st->x || st->y || st->z;
     if (obox && b.pset[1].x)  // skin: a list step's box ids come from its step-start centres
       RUN("readout_box", 1, launch_readout_box(sm, b.pset[s->pos_cur ^ 1], b.skey, s->g, s->blocks_stream));
-    RUN("unsort", 1, launch_unsort(sm, b, A, s->g, pos ? b.sorted.x : nullptr, b.sorted.y, b.sorted.z, odiam, ovol,
-                                   onbr, obox, s->blocks_stream));
-    if (st->x) CK(cudaMemcpyAsync(st->x, b.sorted.x, n * sizeof(double), cudaMemcpyDeviceToHost, sm));
-    if (st->y) CK(cudaMemcpyAsync(st->y, b.sorted.y, n * sizeof(double), cudaMemcpyDeviceToHost, sm));
-    if (st->z) CK(cudaMemcpyAsync(st->z, b.sorted.z, n * sizeof(double), cudaMemcpyDeviceToHost, sm));
+    if (odiam || ovol || onbr || obox)
+      RUN("unsort", 1, launch_unsort(sm, b, A, s->g, nullptr, nullptr, nullptr, odiam, ovol, onbr, obox,
+                                     s->blocks_stream));
+    if (pos) {
+      // each coordinate is permuted into id order, then copied to the host on a second stream
+      // while the next one is permuted
+      if (!s->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+        for (int a = 0; a < 3; ++a) CK(cudaEventCreateWithFlags(&s->axis_done[a], cudaEventDisableTiming));
+      }
+      const double* src[3] = {b.pos.x, b.pos.y, b.pos.z};
+      double* stage[3] = {b.sorted.x, b.sorted.y, b.sorted.z};
+      double* dst[3] = {st->x, st->y, st->z};
+      for (int a = 0; a < 3; ++a) {
+        if (!dst[a]) continue;
+        RUN("unsort_axis", 1, launch_unsort_axis(sm, src[a], A.id, stage[a], s->g, s->blocks_stream));
+        CK(cudaEventRecord(s->axis_done[a], sm));
+        CK(cudaStreamWaitEvent(s->copy_stream, s->axis_done[a], 0));
+        CK(cudaMemcpyAsync(dst[a], stage[a], n * sizeof(double), cudaMemcpyDeviceToHost, s->copy_stream));
+      }
+    }
     if (odiam) CK(cudaMemcpyAsync(st->diameter, odiam, n * sizeof(float), cudaMemcpyDeviceToHost, sm));
     if (ovol) CK(cudaMemcpyAsync(st->volume, ovol, n * sizeof(double), cudaMemcpyDeviceToHost, sm));
     if (onbr) CK(cudaMemcpyAsync(st->neighbour_count, onbr, n * sizeof(unsigned), cudaMemcpyDeviceToHost, sm));
     if (obox) CK(cudaMemcpyAsync(st->box_id, obox, n * sizeof(unsigned), cudaMemcpyDeviceToHost, sm));
     CK(cudaStreamSynchronize(sm));
+    if (pos) CK(cudaStreamSynchronize(s->copy_stream));
     CK(cudaMemcpy(s->gh, s->g, sizeof(DevGrid), cudaMemcpyDeviceToHost));
     if ((rc = decode_err(s, s->gh->err))) return rc;
   }
@@ -932,6 +951,9 @@ void bdm_destroy(bdm_sim* s) {
   if (s->gh) cudaFreeHost(s->gh);
   if (s->err_pinned) cudaFreeHost(s->err_pinned);
   if (s->err_event) cudaEventDestroy(s->err_event);
+  for (int a = 0; a < 3; ++a)
+    if (s->axis_done[a]) cudaEventDestroy(s->axis_done[a]);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   cudaGetLastError();
   delete s;

@@ -335,6 +335,8 @@ void launch_secrete(cudaStream_t s, const MechBuffers& b, DevGrid* g, float* gri
 void launch_unsort(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                    double* ox, double* oy, double* oz, float* odiam, double* ovol,
                    unsigned* onbr, unsigned* obox, int grid_blocks);
+void launch_unsort_axis(cudaStream_t s, const double* src, const unsigned* id, double* dst, DevGrid* g,
+                        int grid_blocks);
 void launch_step_done(cudaStream_t s, DevGrid* g);
 void launch_prepare_agents(cudaStream_t s, unsigned n0, unsigned n, const double* x, const double* y,
                            const double* z, const float* diam, unsigned* id, double* vol,

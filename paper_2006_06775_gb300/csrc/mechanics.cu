@@ -1401,6 +1401,22 @@ __global__ void __launch_bounds__(kBlock) k_unsort(
   }
 }
 
+// Read-out of one coordinate into agent-id order (a read-out of the three runs as three launches, so
+// that each coordinate's copy to the host overlaps the next coordinate's permutation).
+__global__ void __launch_bounds__(kBlock) k_unsort_axis(const double* __restrict__ src,
+                                                        const unsigned* __restrict__ id,
+                                                        double* __restrict__ dst, DevGrid* g) {
+  const unsigned n = g->n;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned i = id[k];
+    if (i >= n) {
+      atomicOr(&g->err, (unsigned)ERR_BOUNDS);
+      continue;
+    }
+    dst[i] = src[k];
+  }
+}
+
 // Upload of new agents (slots n0 .. n0 + n - 1): validate, assign dense ids, derive volumes
 // ((pi/6) d^3 in the order ((pi/6 * d) * d) * d) and clear the per-agent outputs.  The first
 // rejected agent (diameter <= 0, non-finite centre, |centre| >= 1e9 um) is recorded in bad_input.
@@ -1552,6 +1568,11 @@ void launch_unsort(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr
                    unsigned* onbr, unsigned* obox, int grid_blocks) {
   k_unsort<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, attr, b.nbr, b.skey, ox, oy,
                                           oz, odiam, ovol, onbr, obox, g);
+}
+
+void launch_unsort_axis(cudaStream_t s, const double* src, const unsigned* id, double* dst, DevGrid* g,
+                        int grid_blocks) {
+  k_unsort_axis<<<grid_blocks, kBlock, 0, s>>>(src, id, dst, g);
 }
 
 void launch_step_done(cudaStream_t s, DevGrid* g) { k_step_done<<<1, 32, 0, s>>>(g); }
