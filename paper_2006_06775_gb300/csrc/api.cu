@@ -373,6 +373,7 @@ int allocate(bdm_sim* s, size_t n_first, const double* x, const double* y, const
         (rc = dalloc_n(s, &b.start, boxcap + 1)))
       return rc;
     if (s->mixed && (rc = dalloc_n(s, &b.p4, C))) return rc;
+    if ((rc = dalloc_n(s, &b.pack, C))) return rc;
     b.pset[0] = b.pos;
     b.p4set[0] = b.p4;
     if (p.skin > 0.0) {
@@ -539,7 +540,7 @@ int enqueue_mech_step(bdm_sim* s) {
   CK(cudaMemsetAsync(b.tiles[0], 0, sizeof(unsigned long long) * b.max_tiles, st));
   // with a skin, finalize decides on the device whether this step rebuilds: the rebuild kernels
   // then see 0 agents / 0 boxes on list steps, and the two force kernels skip the other kind
-  RUN("key_hist", 1, launch_key_hist(st, b, g, s->blocks_stream));
+  RUN("key_hist", 1, launch_key_hist(st, b, A.id, g, s->blocks_stream));
   RUN("scan_box", 1, launch_scan(st, b.count, b.start, &g->nbox1_sort, b.tiles[0], &g->scan_ctr[0], &g->err,
                                  1, s->blocks_scan));
   RUN("scatter", 1, launch_scatter(st, b, g, s->blocks_stream));

@@ -72,7 +72,7 @@ struct DevGrid {
   unsigned n_step;                // agents the last step moved (a list step's box-id read-out)
   unsigned long long skipped;     // agent evaluations skipped as stationary (list steps)
   unsigned n_eval;                // stationary skip: warps listed for evaluation this step
-  unsigned reserved_eval;
+  unsigned fresh;                 // agents were uploaded since the last step (arbitrary order)
 };
 
 struct MechConsts {               // per-simulation constants passed by value
@@ -255,6 +255,11 @@ struct AgentArrays {             // one SoA buffer of agents
   double* vol;                   // growth only (else nullptr)
 };
 
+struct alignas(32) PackedAgent {  // one agent's centre, id and box in one 32-byte sector
+  double x, y, z;
+  unsigned id, key;
+};
+
 struct MechBuffers {
   AgentArrays pos;               // current positions (x,y,z used); with a skin = pset[current]
   AgentArrays sorted;            // positions gathered into canonical order (x,y,z used)
@@ -265,6 +270,9 @@ struct MechBuffers {
   AgentArrays attr[2];           // diam/id/vol, ping-pong by step parity
   unsigned *key, *rank, *perm, *skey, *nbr, *count, *start;
   float4* p4;                    // mixed: box-relative offsets + radius (= p4set[current])
+  // the first rebuild after an upload: the agents packed by the key kernel, so the gather reads one
+  // sector per agent from the arbitrary upload order instead of one per field
+  PackedAgent* pack;
   unsigned long long* tiles[2];  // scan tile states (box scan, division scan)
   unsigned* flag;                // growth: divide flags by id; also the division rank array
   unsigned* drank;
@@ -290,7 +298,8 @@ struct MechBuffers {
 void launch_bounds(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                    int grid_blocks);
 void launch_finalize(cudaStream_t s, DevGrid* g, MechConsts c);
-void launch_key_hist(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
+void launch_key_hist(cudaStream_t s, const MechBuffers& b, const unsigned* id, DevGrid* g,
+                     int grid_blocks);
 void launch_scan(cudaStream_t s, unsigned* in, unsigned* out, const unsigned* n_items,
                  unsigned long long* tiles, unsigned* tile_ctr, unsigned* err, int zero_input,
                  int grid_blocks);

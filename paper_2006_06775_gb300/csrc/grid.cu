@@ -76,8 +76,11 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(const double* __restrict__ 
                                                      const double* __restrict__ z,
                                                      unsigned* __restrict__ key,
                                                      unsigned* __restrict__ rank,
-                                                     unsigned* __restrict__ count, DevGrid* g) {
+                                                     unsigned* __restrict__ count,
+                                                     const unsigned* __restrict__ id,
+                                                     PackedAgent* __restrict__ pack, DevGrid* g) {
   const unsigned n = g->nbox ? g->n_sort : 0u;
+  const bool packing = pack && g->fresh;
   const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const float inv = g->invLq;
@@ -92,6 +95,15 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(const double* __restrict__ 
     unsigned k = (unsigned)ix + (unsigned)d0 * ((unsigned)iy + (unsigned)d1 * (unsigned)iz);
     key[i] = k;
     rank[i] = atomicAdd(&count[k], 1u);
+    if (packing) {
+      PackedAgent a;
+      a.x = x[i];
+      a.y = y[i];
+      a.z = z[i];
+      a.id = id[i];
+      a.key = k;
+      pack[i] = a;
+    }
   }
 }
 
@@ -123,21 +135,35 @@ __global__ void __launch_bounds__(kBlock) k_gather(
     const unsigned* __restrict__ start, const double* __restrict__ sx,
     const double* __restrict__ sy, const double* __restrict__ sz, AgentArrays src,
     double* __restrict__ dx, double* __restrict__ dy, double* __restrict__ dz, AgentArrays dst,
-    unsigned* __restrict__ skey, float4* __restrict__ p4, DevGrid* g) {
+    unsigned* __restrict__ skey, float4* __restrict__ p4, const PackedAgent* __restrict__ pack,
+    DevGrid* g) {
   const unsigned n = g->nbox ? g->n_sort : 0u;
   const long long O0 = g->O[0], O1 = g->O[1], O2 = g->O[2], Lq = g->Lq;
   const unsigned d0 = (unsigned)g->dims[0], d1 = (unsigned)g->dims[1];
+  const bool packed = pack && g->fresh;  // the same for every thread
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned s = perm[k];
-    const unsigned b = key[s];
+    PackedAgent a;
+    if (packed) {
+      a = pack[s];
+    } else {
+      a.key = key[s];
+      a.id = src.id[s];
+    }
+    const unsigned b = a.key;
     const unsigned lo = start[b], hi = start[b + 1];
-    const unsigned myid = src.id[s];
+    const unsigned myid = a.id;
     unsigned d = lo;
     if (hi - lo > 1) {
       for (unsigned m = lo; m < hi; ++m)
-        if (m != k) d += src.id[perm[m]] < myid ? 1u : 0u;
+        if (m != k) d += (packed ? pack[perm[m]].id : src.id[perm[m]]) < myid ? 1u : 0u;
     }
-    const double x = sx[s], y = sy[s], z = sz[s];
+    if (!packed) {
+      a.x = sx[s];
+      a.y = sy[s];
+      a.z = sz[s];
+    }
+    const double x = a.x, y = a.y, z = a.z;
     const float di = src.diam[s];
     dx[d] = x;
     dy[d] = y;
@@ -165,8 +191,10 @@ void launch_bounds(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr
 
 void launch_finalize(cudaStream_t s, DevGrid* g, MechConsts c) { k_finalize<<<1, 32, 0, s>>>(g, c); }
 
-void launch_key_hist(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks) {
-  k_key_hist<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, b.key, b.rank, b.count, g);
+void launch_key_hist(cudaStream_t s, const MechBuffers& b, const unsigned* id, DevGrid* g,
+                     int grid_blocks) {
+  k_key_hist<<<grid_blocks, kBlock, 0, s>>>(b.pos.x, b.pos.y, b.pos.z, b.key, b.rank, b.count, id,
+                                            b.pack, g);
 }
 
 void launch_scan(cudaStream_t s, unsigned* in, unsigned* out, const unsigned* n_items,
@@ -184,11 +212,11 @@ void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_
   if (mixed)
     k_gather<true><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
                                                   b.pos.z, src_attr, b.sorted.x, b.sorted.y,
-                                                  b.sorted.z, dst_attr, b.skey, b.p4, g);
+                                                  b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
   else
     k_gather<false><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
                                                    b.pos.z, src_attr, b.sorted.x, b.sorted.y,
-                                                   b.sorted.z, dst_attr, b.skey, b.p4, g);
+                                                   b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
 }
 
 }  // namespace bdm

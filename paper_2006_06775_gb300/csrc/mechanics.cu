@@ -1425,6 +1425,7 @@ __global__ void __launch_bounds__(kBlock) k_prepare_agents(
     const double* __restrict__ z, const float* __restrict__ diam, unsigned* __restrict__ id,
     double* __restrict__ vol, int derive_volume, unsigned* __restrict__ nbr,
     unsigned* __restrict__ skey, DevGrid* g) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) g->fresh = 1u;  // the next rebuild gathers packed agents
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned i = n0 + k;
     const double px = x[i], py = y[i], pz = z[i];
@@ -1442,7 +1443,10 @@ __global__ void __launch_bounds__(kBlock) k_prepare_agents(
 }
 
 __global__ void k_step_done(DevGrid* g) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) g->step += 1ull;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    g->step += 1ull;
+    g->fresh = 0u;
+  }
 }
 
 // ---- launch wrappers -------------------------------------------------------------------------
