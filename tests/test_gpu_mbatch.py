@@ -118,3 +118,27 @@ def test_pool_rejects_bad_loads():
     check_equal(pool.get_state(1), single(params, inp, 1), 1)
     check_equal(pool.get_state(0), single(params, inp, 2), 0)
     pool.close()
+
+
+def test_pool_edge_sizes_and_idle_steps():
+    """A one-agent simulation and one at exactly the slot capacity; steps with no active slot are
+    no-ops; a slot keeps its state after reaching its target while others still step."""
+    pool = bdm.MechBatch("mixed", slots=3, slot_capacity=2000)
+    pool.step(3)  # nothing loaded: nothing happens
+    assert list(pool.poll()) == [-1, -1, -1]
+    params, inp = synth.served_mechanics(2000, 11)
+    one = {k: v[:1].copy() for k, v in inp.items() if hasattr(v, "__len__")}
+    pool.load_sim(0, params, one["x"], one["y"], one["z"], one["diameter"], 4)
+    pool.load_sim(2, params, inp["x"], inp["y"], inp["z"], inp["diameter"], 9)
+    pool.step(6)
+    assert list(pool.poll()) == [4, -1, 6]
+    check_equal(pool.get_state(0), single(params, one, 4), "one agent")
+    pool.step(5)
+    assert list(pool.poll()) == [4, -1, 9]
+    check_equal(pool.get_state(2), single(params, inp, 9), "full slot")
+    check_equal(pool.get_state(0), single(params, one, 4), "one agent, after others stepped")
+    pool.release(0)
+    pool.release(2)
+    pool.step(2)
+    assert list(pool.poll()) == [-1, -1, -1]
+    pool.close()
