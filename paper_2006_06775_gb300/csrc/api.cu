@@ -544,7 +544,7 @@ int enqueue_mech_step(bdm_sim* s) {
   RUN("scan_box", 1, launch_scan(st, b.count, b.start, &g->nbox1_sort, b.tiles[0], &g->scan_ctr[0], &g->err,
                                  1, s->blocks_scan));
   RUN("scatter", 1, launch_scatter(st, b, g, s->blocks_stream));
-  RUN("gather", 1, launch_gather(st, b, A, B, g, s->mixed, s->blocks_stream));
+  RUN("gather", 1, launch_gather(st, b, A, B, g, s->mixed, s->mc.skin > 0.0, s->blocks_stream));
   if (s->mc.skin > 0.0) {
     RUN("attr_copy", 1, launch_attr_copy(st, B, A, g, s->blocks_stream));
     RUN("list_build", 1, launch_list_build(st, b, g, s->blocks_list));

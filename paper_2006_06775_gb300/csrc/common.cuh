@@ -305,7 +305,7 @@ void launch_scan(cudaStream_t s, unsigned* in, unsigned* out, const unsigned* n_
                  int grid_blocks);
 void launch_scatter(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_blocks);
 void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_attr,
-                   const AgentArrays& dst_attr, DevGrid* g, bool mixed, int grid_blocks);
+                   const AgentArrays& dst_attr, DevGrid* g, bool mixed, bool xsort, int grid_blocks);
 // mechanics.cu
 void launch_force(cudaStream_t s, const MechBuffers& b, const AgentArrays& attr, DevGrid* g,
                   MechConsts c, bool mixed, int grid_blocks);

@@ -129,7 +129,11 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const unsigned* __restrict__
 // Canonicalise and gather: the arrival order inside a box is replaced by ascending id (R6), and the
 // agent payload moves into the canonical order.  The mixed-precision path also writes each agent's
 // FP32 offset from its box's lower corner (exact lattice difference, then one rounding) and radius.
-template <bool MIXED>
+// With neighbour lists (XSORT) a box's agents are ordered by their lattice x coordinate instead, ties
+// by id: a row of three boxes is then sorted along x, and the list build stops walking a row where
+// its candidates leave the agent's x window.  The lists' order (and so the FP32 force sums) follows
+// this order; counts and box ids do not depend on it.
+template <bool MIXED, bool XSORT>
 __global__ void __launch_bounds__(kBlock) k_gather(
     const unsigned* __restrict__ perm, const unsigned* __restrict__ key,
     const unsigned* __restrict__ start, const double* __restrict__ sx,
@@ -153,15 +157,28 @@ __global__ void __launch_bounds__(kBlock) k_gather(
     const unsigned b = a.key;
     const unsigned lo = start[b], hi = start[b + 1];
     const unsigned myid = a.id;
-    unsigned d = lo;
-    if (hi - lo > 1) {
-      for (unsigned m = lo; m < hi; ++m)
-        if (m != k) d += (packed ? pack[perm[m]].id : src.id[perm[m]]) < myid ? 1u : 0u;
-    }
     if (!packed) {
       a.x = sx[s];
       a.y = sy[s];
       a.z = sz[s];
+    }
+    unsigned d = lo;
+    if (hi - lo > 1) {
+      if (XSORT) {
+        // x order through the order-preserving integer encoding (the lattice x, and so the FP32
+        // offset, never decreases along it)
+        const unsigned long long qm = enc_double(a.x);
+        for (unsigned m = lo; m < hi; ++m) {
+          if (m == k) continue;
+          const unsigned s2 = perm[m];
+          const unsigned long long q2 = enc_double(packed ? pack[s2].x : sx[s2]);
+          const unsigned id2 = packed ? pack[s2].id : src.id[s2];
+          d += (q2 < qm || (q2 == qm && id2 < myid)) ? 1u : 0u;
+        }
+      } else {
+        for (unsigned m = lo; m < hi; ++m)
+          if (m != k) d += (packed ? pack[perm[m]].id : src.id[perm[m]]) < myid ? 1u : 0u;
+      }
     }
     const double x = a.x, y = a.y, z = a.z;
     const float di = src.diam[s];
@@ -208,15 +225,19 @@ void launch_scatter(cudaStream_t s, const MechBuffers& b, DevGrid* g, int grid_b
 }
 
 void launch_gather(cudaStream_t s, const MechBuffers& b, const AgentArrays& src_attr,
-                   const AgentArrays& dst_attr, DevGrid* g, bool mixed, int grid_blocks) {
-  if (mixed)
-    k_gather<true><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
-                                                  b.pos.z, src_attr, b.sorted.x, b.sorted.y,
-                                                  b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
+                   const AgentArrays& dst_attr, DevGrid* g, bool mixed, bool xsort, int grid_blocks) {
+  if (mixed && xsort)
+    k_gather<true, true><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
+                                                        b.pos.z, src_attr, b.sorted.x, b.sorted.y,
+                                                        b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
+  else if (mixed)
+    k_gather<true, false><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
+                                                         b.pos.z, src_attr, b.sorted.x, b.sorted.y,
+                                                         b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
   else
-    k_gather<false><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
-                                                   b.pos.z, src_attr, b.sorted.x, b.sorted.y,
-                                                   b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
+    k_gather<false, false><<<grid_blocks, kBlock, 0, s>>>(b.perm, b.key, b.start, b.pos.x, b.pos.y,
+                                                          b.pos.z, src_attr, b.sorted.x, b.sorted.y,
+                                                          b.sorted.z, dst_attr, b.skey, b.p4, b.pack, g);
 }
 
 }  // namespace bdm

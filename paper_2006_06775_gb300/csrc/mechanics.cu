@@ -554,32 +554,45 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
         for (int u = 0; u < 4; ++u)
           q[u] = k0 + (unsigned)u < m ? __ldg(p4 + (v[u] >> 5)) : make_float4(3.0e4f, 3.0e4f, 3.0e4f, 0.f);
         // the four entries are evaluated without branches (a slot past the list is far away, so it
-        // neither counts nor touches); their contributions are added in list order
+        // neither counts nor touches), two at a time through the paired FP32 instructions (the same
+        // per-component rounding as the scalar ones); contributions are added in list order
+        const float2 pxy = make_float2(pi.x, pi.y), m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const unsigned cc = v[u] & 31u;
-          const float4 sh = s_shift[k0 + (unsigned)u < m ? cc : 13u];
-          const float ex = (pi.x + sh.x) - q[u].x;
-          const float ey = (pi.y + sh.y) - q[u].y;
-          const float ez = (pi.z + sh.z) - q[u].z;
-          const float dd = pair_d2(ex, ey, ez);
-          cnt += dd < R2lo ? 1u : 0u;
-          if (dd >= R2lo && dd <= R2hi) {  // near R: queued for the FP64 decision after the loop
-            if (nband < (unsigned)kBQ) s_bq[nband][t] = v[u] >> 5;
-            ++nband;
+        for (int hh = 0; hh < 2; ++hh) {
+          const int a = 2 * hh, b = 2 * hh + 1;
+          const float4 sa = s_shift[k0 + (unsigned)a < m ? v[a] & 31u : 13u];
+          const float4 sb = s_shift[k0 + (unsigned)b < m ? v[b] & 31u : 13u];
+          const float2 exa = __ffma2_rn(make_float2(q[a].x, q[a].y), m1, __fadd2_rn(pxy, make_float2(sa.x, sa.y)));
+          const float2 exb = __ffma2_rn(make_float2(q[b].x, q[b].y), m1, __fadd2_rn(pxy, make_float2(sb.x, sb.y)));
+          const float eza = (pi.z + sa.z) - q[a].z, ezb = (pi.z + sb.z) - q[b].z;
+          const float2 dd = make_float2(pair_d2(exa.x, exa.y, eza), pair_d2(exb.x, exb.y, ezb));
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float d = e ? dd.y : dd.x;
+            cnt += d < R2lo ? 1u : 0u;
+            if (d >= R2lo && d <= R2hi) {  // near R: queued for the FP64 decision after the loop
+              if (nband < (unsigned)kBQ) s_bq[nband][t] = v[e ? b : a] >> 5;
+              ++nband;
+            }
           }
-          const float rs = pi.w + q[u].w;
-          const float rinv = rsqrtf(dd);
-          const float delta = rs - dd * rinv;
-          // sqrt(rho delta) = sqrt(ri rj delta / rs) = p rsqrt(p rs) with p = ri rj delta: one
-          // reciprocal square root instead of a reciprocal and a reciprocal square root
-          const float pp = (pi.w * q[u].w) * delta;
-          const float F = c.kf * delta - c.gammaf * (pp * rsqrtf(pp * rs));
-          const float sc = F * rinv;
-          const bool touch = dd <= R2hi && dd < rs * rs && dd > 0.f && delta > 0.f;
-          Fx = touch ? fmaf(sc, ex, Fx) : Fx;
-          Fy = touch ? fmaf(sc, ey, Fy) : Fy;
-          Fz = touch ? fmaf(sc, ez, Fz) : Fz;
+          const float2 rs = make_float2(pi.w + q[a].w, pi.w + q[b].w);
+          const float2 rinv = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
+          const float2 delta = __ffma2_rn(make_float2(-dd.x, -dd.y), rinv, rs);
+          // sqrt(rho delta) = sqrt(ri rj delta / rs) = p rsqrt(p rs) with p = ri rj delta
+          const float2 pp = __fmul2_rn(make_float2(pi.w * q[a].w, pi.w * q[b].w), delta);
+          const float2 tt = __fmul2_rn(pp, rs);
+          const float2 gv = __fmul2_rn(make_float2(c.gammaf, c.gammaf),
+                                       __fmul2_rn(pp, make_float2(rsqrtf(tt.x), rsqrtf(tt.y))));
+          const float2 sc = __fmul2_rn(__ffma2_rn(make_float2(c.kf, c.kf), delta, make_float2(-gv.x, -gv.y)), rinv);
+          const float2 rs2 = __fmul2_rn(rs, rs);
+          const bool ta = dd.x <= R2hi && dd.x < rs2.x && dd.x > 0.f && delta.x > 0.f;
+          const bool tb = dd.y <= R2hi && dd.y < rs2.y && dd.y > 0.f && delta.y > 0.f;
+          Fx = ta ? fmaf(sc.x, exa.x, Fx) : Fx;
+          Fy = ta ? fmaf(sc.x, exa.y, Fy) : Fy;
+          Fz = ta ? fmaf(sc.x, eza, Fz) : Fz;
+          Fx = tb ? fmaf(sc.y, exb.x, Fx) : Fx;
+          Fy = tb ? fmaf(sc.y, exb.y, Fy) : Fy;
+          Fz = tb ? fmaf(sc.y, ezb, Fz) : Fz;
         }
       }
       if (nband > (unsigned)kBQ) {
