@@ -308,12 +308,12 @@ __global__ void __launch_bounds__(kFT, 3) k_force_mixed(
 
 // ---------------------------------------------------------------------------------------------
 // Neighbour-list steps (skin > 0).  A rebuild step lists, per agent, every candidate within R + skin
-// found by the canonical 27-box walk on a grid whose box length is at least R + skin
-// ((j << 5) | (row * 3 + box x), in canonical order: k_list_build).  Every step then evaluates the
+// found by the 27-box walk on a grid whose box length is at least R + skin ((j << 5) |
+// (row * 3 + box x), in the rebuild's box order: k_list_build).  Every step then evaluates the
 // lists (k_force_skin<false>): while no agent has moved more than skin / 2 since the rebuild, every
 // pair within R was within R + skin at the rebuild, so every neighbour and contact is listed.
 // Counts use the same FP32 band + FP64 decision as the walk, so they stay exact; the FP32 force sums
-// follow the list (the canonical order of the last rebuild).  If a list overflowed, that step's
+// follow the list (the box order of the last rebuild).  If a list overflowed, that step's
 // forces come from the walk itself (k_force_skin<true>) and the next step rebuilds.  Both apply the
 // capped displacement themselves, into the other of two alternating position sets.
 // ---------------------------------------------------------------------------------------------
@@ -353,7 +353,7 @@ __device__ __noinline__ unsigned list_rescan(unsigned i, unsigned m, const unsig
 // the kernel reads the current set and writes the next, so every neighbour read sees step-start
 // values while each agent's own update is written at once (no separate update pass).  On a rebuild
 // step the centres come from the gather's set and the offsets from the current set's offset buffer,
-// which the gather has overwritten in canonical order.
+// which the gather has overwritten in box order.
 template <bool BUILD, bool SKIP = false>
 __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
     const double* __restrict__ gx, const double* __restrict__ gy, const double* __restrict__ gz,
@@ -689,13 +689,13 @@ __global__ void __launch_bounds__(kFT, BUILD ? 3 : 4) k_force_skin(
   if (t == 0 && s_dmax) atomicMax(&g->max_disp, s_dmax);
 }
 
-// Lists of a rebuild step: the canonical 27-box walk on a grid of box length >= R + skin, keeping
+// Lists of a rebuild step: the 27-box walk on a grid of box length >= R + skin, keeping
 // every candidate within R + skin (no forces; the list kernel computes them from the lists).  The
-// nine row runs of an agent (each its boxes x-1, x, x+1, contiguous in the canonical order) are
+// nine row runs of an agent (each its boxes x-1, x, x+1, contiguous in the box order) are
 // first collected into a per-thread table in shared memory, all 36 run bounds loaded at once; the
 // candidates of all runs are then visited in ONE loop, so a warp's lanes, whose runs differ in
 // length, wait only for the lane with the most candidates in total rather than for the longest run
-// of every row.  Entries are written in the canonical order.
+// of every row.  Entries are written in the box order (boxes by key, a box's agents along x).
 constexpr int kLB = 256;  // threads per block of the list build
 
 __global__ void __launch_bounds__(kLB) k_list_build(const float4* __restrict__ p4,
