@@ -380,7 +380,7 @@ def run_ours(args):
     sim.close()
     ensemble = serving = plain = spheroid = stationary = oncology = neurite = mech_pool = None
     if rank == 0 and args.neurite_agents > 0:
-        neurite = bench_neurite(args.neurite_agents)
+        neurite = bench_neurite(args.neurite_agents, skin=args.neurite_skin)
     if rank == 0 and not args.no_small:
         plain = bench_plain()
         spheroid = bench_spheroid()
@@ -608,10 +608,14 @@ NEURITE_BYTES_PER_AGENT = 92  # state read once (position 24, diameter 8, rest 8
                               # offset 24) + position written (24)
 NEURITE_FORCE_BYTES_PER_AGENT = 92  # own record (40) + spring and bound (16) + key (4) read,
                                     # output record (32) written
+# with neighbour lists the force kernel reads its own records (16 + 32), spring and bound (16), list
+# length (4) and 4 B per listed entry, and writes the output record (32)
+NEURITE_LIST_BYTES_PER_AGENT = lambda m: 100 + 4 * m
+NEURITE_SKIN = 1.0  # neighbour-list skin (um) of the neuron-forest benchmark
 
 
 def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_steps=2,
-                  oracle_sample=20_000):
+                  oracle_sample=20_000, skin=NEURITE_SKIN):
     """Neurite mechanics on the neuron forest (somata with apical and basal dendrite trees, the
     large pyramidal-cell run's 5000 cells and 9e6 agents), mixed precision: `steps` steps after
     `warmup`, timed on the device; per-kernel times from a separately profiled step; the FP64 check
@@ -626,32 +630,41 @@ def bench_neurite(n_agents=9_000_000, neurons=5000, steps=10, warmup=3, fp64_ste
     out = {"workload": "neuron forest: %d somata (10 um) with 1 apical + 3 basal dendrite trees, "
                        "%d agents, %.0f um cube, branching 0.038 / 0.006 per generation"
                        % (neurons, n, side),
-           "agents": n, "steps": steps, "warmup": warmup, "precision": "mixed"}
+           "agents": n, "steps": steps, "warmup": warmup, "precision": "mixed", "skin_um": skin}
     params = dict(params, capacity=n, box_capacity=4 * n + 4096)
-    sim = bdm.Neurite(dict(params, precision="mixed"))
+    sim = bdm.Neurite(dict(params, precision="mixed", skin=skin))
     sim.set_agents(inp)
     sim.step(warmup)
+    rb0 = sim.list_info()[0]
     ms = _event_time_ms(sim.stream, lambda: sim.step(steps))
+    rb1, entries = sim.list_info()
     st = sim.get_state()
+    # per-kernel times over as many steps as were timed (list and rebuild steps in their mix)
     sim.profile(True)
-    sim.step(2)
+    sim.step(steps)
     kt = sim.kernel_times()
     sim.profile(False)
     sim.close()
     per = {k: v[1] / v[0] for k, v in kt.items()}
     peak, peak_kind = load_peaks()
-    fms = per.get("nr_force", float("nan"))
-    achieved = NEURITE_FORCE_BYTES_PER_AGENT * n / (fms * 1e-3) / 1e9
+    if skin > 0.0:
+        fkernel = "nr_force_list"
+        fbytes = NEURITE_LIST_BYTES_PER_AGENT(entries / n)
+        out.update({"rebuilds_in_timed_steps": rb1 - rb0, "list_entries_per_agent": entries / n})
+    else:
+        fkernel, fbytes = "nr_force", NEURITE_FORCE_BYTES_PER_AGENT
+    fms = per.get(fkernel, float("nan"))
+    achieved = fbytes * n / (fms * 1e-3) / 1e9
     step_achieved = NEURITE_BYTES_PER_AGENT * n / (ms / steps * 1e-3) / 1e9
     out.update({"ms_per_step": ms / steps, "agent_steps_per_s": n * steps / (ms * 1e-3),
                 "neighbours_per_agent": float(np.mean(st["neighbour_count"])),
                 "L_um": st["L"],
                 "kernels_ms_per_launch": {k: round(v, 4) for k, v in per.items()},
-                "roofline": {"bound": "hbm", "kernel": "nr_force", "achieved": achieved,
+                "roofline": {"bound": "hbm", "kernel": fkernel, "achieved": achieved,
                              "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                             "peak_kind": peak_kind,
-                             "alg_bytes_per_agent": NEURITE_FORCE_BYTES_PER_AGENT,
-                             "traffic": measured_traffic("nr_force", n)},
+                             "peak_kind": peak_kind, "kernel_ms": fms,
+                             "alg_bytes_per_agent": fbytes,
+                             "traffic": measured_traffic(fkernel, n)},
                 "step_roofline": {"bytes_per_agent_step": NEURITE_BYTES_PER_AGENT,
                                   "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                                   "frac": step_achieved / peak}})
@@ -870,6 +883,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--neurite-agents", type=int, default=9_000_000,
                     help="agents of the neuron-forest sub-benchmark (0: skip it)")
+    ap.add_argument("--neurite-skin", type=float, default=NEURITE_SKIN,
+                    help="neighbour-list skin (um) of the neuron-forest sub-benchmark (0: rebuild every step)")
     ap.add_argument("--neurite-only", action="store_true",
                     help="run only the neuron-forest sub-benchmark and print its object")
     args = ap.parse_args()
@@ -879,7 +894,8 @@ def main():
         return run_reference(args)
     if args.neurite_only:
         print(json.dumps({"neurite": bench_neurite(args.neurite_agents, steps=args.steps,
-                                                   warmup=args.warmup)}), flush=True)
+                                                   warmup=args.warmup, skin=args.neurite_skin)}),
+              flush=True)
         return 0
     return run_ours(args)
 

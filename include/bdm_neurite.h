@@ -57,6 +57,16 @@ typedef struct bdm_neurite_params {
   uint64_t box_capacity;       /* grid boxes; 0 = 2 * capacity + 4096.  A step whose grid needs
                                   more fails with BDM_ENOMEM at the next synchronising call       */
   void* stream;                /* cudaStream_t, NULL = a stream the handle creates               */
+  double skin;                 /* >= 0.  BDM_MIXED only: 0 = the grid is rebuilt every step (the
+                                  paper's cadence); > 0 = neighbour lists.  A rebuild step bins
+                                  the agents on boxes of L + skin and lists, per agent, every
+                                  other agent whose binning point lies within L + skin; the steps
+                                  after it evaluate the lists (same counts, contacts and update)
+                                  until a binning point may have moved more than
+                                  (skin - (L - L_rebuild)) / 2 since the rebuild (the summed
+                                  displacement of the agent's own point bounds that of its
+                                  binning point), after 64 steps, or after set_agents.  The FP32
+                                  contact sums then follow the list order of the last rebuild.  */
 } bdm_neurite_params;
 
 typedef struct bdm_neurite bdm_neurite;
@@ -82,6 +92,11 @@ int bdm_neurite_step(bdm_neurite* s, int n);
  * Before the first step after bdm_neurite_set_agents the counts and L read 0. */
 int bdm_neurite_get_state(bdm_neurite* s, size_t* n_out, double* x, double* y, double* z,
                           uint32_t* neighbour_count, double* L_out);
+
+/* Neighbour-list bookkeeping (skin > 0; synchronises the stream): rebuilds since the last
+ * bdm_neurite_set_agents (or NULL) and the entries listed by the last rebuild (or NULL).  Both
+ * read 0 without a skin. */
+int bdm_neurite_list_info(bdm_neurite* s, uint64_t* rebuilds, uint64_t* entries);
 
 /* Per-kernel CUDA-event timing of later steps (as bdm_profile / bdm_kernel_times). */
 int bdm_neurite_profile(bdm_neurite* s, int enable);

@@ -82,7 +82,7 @@ class NeuriteParams(ctypes.Structure):
                 ("attraction", ctypes.c_double), ("max_displacement", ctypes.c_double),
                 ("spring", ctypes.c_double), ("interaction_radius", ctypes.c_double),
                 ("capacity", ctypes.c_uint64), ("box_capacity", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("skin", ctypes.c_double)]
 
 
 _lib = None
@@ -146,6 +146,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.bdm_neurite_get_state.argtypes = [vp, ctypes.POINTER(sz), vp, vp, vp, vp,
                                         ctypes.POINTER(ctypes.c_double)]
     L.bdm_neurite_profile.argtypes = [vp, i32]
+    L.bdm_neurite_list_info.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]
     L.bdm_neurite_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime), i32,
                                            ctypes.POINTER(i32)]
     L.bdm_neurite_destroy.argtypes = [vp]
@@ -631,7 +633,7 @@ class Neurite:
         p.struct_size = ctypes.sizeof(NeuriteParams)
         p.precision = BDM_MIXED if self.params.get("precision", "mixed") == "mixed" else BDM_FP64
         for k in ("dt", "repulsion", "attraction", "max_displacement", "spring",
-                  "interaction_radius"):
+                  "interaction_radius", "skin"):
             setattr(p, k, float(self.params.get(k, 0.0)))
         p.capacity = int(self.params.get("capacity", 1 << 20))
         # grid room for arbors that spread well beyond their somata (the library's own default,
@@ -685,6 +687,12 @@ class Neurite:
 
     def profile(self, enable=True):
         self._check(load().bdm_neurite_profile(self.h, 1 if enable else 0))
+
+    def list_info(self):
+        """(rebuilds so far, entries listed by the last rebuild); both 0 without a skin."""
+        rb, ent = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        self._check(load().bdm_neurite_list_info(self.h, ctypes.byref(rb), ctypes.byref(ent)))
+        return int(rb.value), int(ent.value)
 
     def kernel_times(self):
         arr = (KernelTime * 64)()

@@ -21,6 +21,10 @@
 //   k_nr_update    id order: own share + daughters' passed-up shares (ascending daughter id),
 //                  capped displacement (mixed: FP32, then one FP64 add per axis), new FP64
 //                  positions (ping-pong)
+// With a skin (mixed precision) the finalize kernel decides on the device whether the step
+// rebuilds: a rebuild step bins on boxes of L + skin and k_nr_list_build lists every agent within
+// L + skin of each slot; on the other steps k_nr_key and the scan do nothing, the scatter refreshes
+// the records in the slots of the last rebuild, and k_nr_force_list evaluates the lists.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,6 +52,9 @@ constexpr int kNrList = 24;           // contact candidates a thread defers to t
 constexpr unsigned kNrSlotBits = 27;  // mixed path: slot index bits of a deferred entry
 constexpr int kNrMaxPartials = 2048;  // blocks of the prepare kernel (one bounds record each)
 constexpr int kNrPartialWords = 7;    // min xyz, max xyz, largest extent
+constexpr unsigned kNrListCap = 128;   // listed agents per slot (skin > 0)
+constexpr unsigned kNrListFull = 0xFFFFFFFFu;  // list length of a slot whose list overflowed
+constexpr unsigned kNrMaxCadence = 64;  // a rebuild at least every 64 steps
 
 struct NrGrid {
   double origin[3];
@@ -57,6 +64,16 @@ struct NrGrid {
   unsigned nbox, nbox1;
   unsigned scan_ctr[2];
   unsigned err;
+  // neighbour lists (mixed precision, skin > 0), decided by the finalize kernel every step
+  double L_list;               // L of the last rebuild
+  unsigned rebuild;            // 1: this step rebuilds the grid and the lists
+  unsigned nbox1_sort;         // items of this step's box scan (nbox + 1, or 0 on list steps)
+  unsigned list_valid;         // the lists describe the current agents (cleared by set_agents)
+  unsigned since_rebuild;      // steps since the last rebuild
+  unsigned max_disp;           // float bits: largest summed move of a point since the rebuild
+  float list_L2f;              // (L_list + skin)^2, widened by 2^-10
+  unsigned pad2;
+  unsigned long long rebuilds, list_entries;
 };
 
 struct alignas(32) Dbl4 {
@@ -283,9 +300,15 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_prepare(
 }
 
 // One block of kNrBlock threads: reduces the prepare kernel's bounds records and sets up the grid.
+// With a skin it first decides whether the step rebuilds: every pair of binning points within L
+// now was within L + 2 m at the last rebuild, m the largest summed move of an agent's point since
+// then (a binning point, a soma's centre or an element's midpoint, moves at most as far as the
+// points that define it), so while 2 m + L - L_rebuild <= skin the lists hold every neighbour and
+// every contact, and the grid and slots of the rebuild stay.
 __global__ void __launch_bounds__(kNrBlock) k_nr_finalize(const double* __restrict__ partials,
                                                           int nblk, unsigned n, double R,
-                                                          unsigned long long box_cap, NrGrid* g) {
+                                                          unsigned long long box_cap, double skin,
+                                                          NrGrid* g) {
   __shared__ double s_red[kNrBlock / 32][kNrPartialWords];
   double v[kNrPartialWords] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
   for (int b = threadIdx.x; b < nblk; b += blockDim.x)
@@ -316,13 +339,37 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_finalize(const double* __restri
   const double L = fmax(R, s_v[6]);
   g->L = L;
   g->L2 = __dmul_rn(L, L);
-  g->nbox = 0;
-  g->nbox1 = 0;
+  g->L2lo = (float)(g->L2 * (1.0 - 0x1p-14));
+  g->L2hi = (float)(g->L2 * (1.0 + 0x1p-14));
   if (n == 0 || !(L > 0.0) || !isfinite(L)) {
+    g->nbox = 0;
+    g->nbox1 = 0;
+    g->nbox1_sort = 0;
+    g->rebuild = 0;
     if (n) g->err |= ERR_RADIUS;
     return;
   }
-  const double Lbox = L * (1.0 + 0x1p-20);
+  if (skin > 0.0) {
+    if (g->list_valid && g->nbox != 0 && g->since_rebuild + 1u < kNrMaxCadence &&
+        2.0 * (double)__uint_as_float(g->max_disp) + (L - g->L_list) <= skin * (1.0 - 1e-6)) {
+      g->rebuild = 0u;  // a list step: the grid and the slots of the last rebuild stay
+      g->nbox1_sort = 0u;
+      g->since_rebuild += 1u;
+      return;
+    }
+    g->L_list = L;
+    g->list_valid = 1u;
+    g->max_disp = 0u;
+    g->since_rebuild = 0u;
+    g->rebuilds += 1ull;
+    g->list_entries = 0ull;
+    g->list_L2f = (float)((L + skin) * (L + skin)) * (1.0f + 1.0f / 1024.0f);
+  }
+  g->rebuild = 1u;
+  g->nbox = 0;
+  g->nbox1 = 0;
+  g->nbox1_sort = 0;
+  const double Lbox = (L + skin) * (1.0 + 0x1p-20);
   double nb = 1.0;
   int dims[3];
   for (int k = 0; k < 3; ++k) {
@@ -346,10 +393,9 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_finalize(const double* __restri
   g->Lbox = Lbox;
   g->invLbox = 1.0 / Lbox;
   g->Lf = (float)Lbox;
-  g->L2lo = (float)(g->L2 * (1.0 - 0x1p-14));
-  g->L2hi = (float)(g->L2 * (1.0 + 0x1p-14));
   g->nbox = (unsigned)nb;
   g->nbox1 = (unsigned)nb + 1u;
+  g->nbox1_sort = (unsigned)nb + 1u;
 }
 
 // Box coordinate: (v - o) / Lbox by the reciprocal.  Its error (a few ulp of at most `dims` box
@@ -366,7 +412,7 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_key(unsigned n, const double* _
                                                      const NrGrid* g, unsigned* __restrict__ key,
                                                      unsigned* __restrict__ rank,
                                                      unsigned* __restrict__ count) {
-  if (g->nbox == 0) return;
+  if (g->nbox == 0 || !g->rebuild) return;  // a list step keeps the keys and ranks of the rebuild
   const double invL = g->invLbox;
   const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const double o0 = g->origin[0], o1 = g->origin[1], o2 = g->origin[2];
@@ -634,16 +680,261 @@ __global__ void __launch_bounds__(kNrForceBlock, MIXED ? 8 : 1) k_nr_force(
   }
 }
 
+// Neighbour lists (mixed precision, skin > 0).  Slot t's list holds the slots u != t whose binning
+// points lie within L + skin of t's (FP32 box-relative offsets, the radius widened by 2^-10), each
+// as u | (box code << 27) in the sweep's order (rows by z then y, boxes by x, slots ascending);
+// the entries of 32 consecutive slots are interleaved (entry k of slot t at (t / 32) 32 cap +
+// 32 k + t % 32) so that entry k of a warp's slots is one line.
+__device__ __forceinline__ size_t nr_list_at(unsigned t, unsigned k) {
+  return (size_t)(t >> 5) * (32u * kNrListCap) + (size_t)k * 32u + (t & 31u);
+}
+
+// A rebuild step's lists: the 27 boxes around each slot (9 runs of 3 boxes adjacent in x), as the
+// sweep visits them.  A slot with more than kNrListCap entries (in a dense region) gets the length
+// kNrListFull: the list kernel sweeps its boxes every step instead.
+__global__ void __launch_bounds__(kNrForceBlock) k_nr_list_build(
+    unsigned n, const unsigned* __restrict__ start, const unsigned* __restrict__ key, NrGrid* g,
+    NrRecords rec, unsigned* __restrict__ list, unsigned* __restrict__ list_n) {
+  if (g->nbox == 0 || !g->rebuild) return;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const float Lf = g->Lf, LL2 = g->list_L2f;
+  unsigned listed = 0u;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = rec.RB[t].C.x;
+    const unsigned kb = key[i];
+    const int ix = (int)(kb % (unsigned)d0), iy = (int)((kb / (unsigned)d0) % (unsigned)d1),
+              iz = (int)(kb / ((unsigned)d0 * (unsigned)d1));
+    const float4 Ai = rec.A32[t];
+    const int x0 = max(ix - 1, 0), x1 = min(ix + 1, d0 - 1);
+    unsigned ln = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int bz2 = iz + dz;
+      if (bz2 < 0 || bz2 >= d2) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int by2 = iy + dy;
+        if (by2 < 0 || by2 >= d1) continue;
+        const unsigned row = (unsigned)d0 * ((unsigned)by2 + (unsigned)d1 * (unsigned)bz2) + (unsigned)x0;
+        const int nb = x1 - x0 + 1;
+        const unsigned s0 = start[row], s1 = start[row + 1];
+        const unsigned s2 = nb >= 2 ? start[row + 2] : s1;
+        const unsigned s3 = nb >= 3 ? start[row + 3] : s2;
+        const float ey = Ai.y - (float)dy * Lf, ez = Ai.z - (float)dz * Lf;
+        int bxc = 0;
+        unsigned nxt = s1;
+        float ex = Ai.x - (float)(x0 - ix) * Lf;
+        float4 An = s0 < s3 ? rec.A32[s0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (unsigned u = s0; u < s3; ++u) {
+          const float4 A = An;
+          if (u + 1 < s3) An = rec.A32[u + 1];
+          while (u >= nxt) {
+            ++bxc;
+            nxt = bxc == 1 ? s2 : s3;
+            ex = Ai.x - (float)(x0 + bxc - ix) * Lf;
+          }
+          const float e0 = ex - A.x, e1 = ey - A.y, e2 = ez - A.z;
+          const float d2f = (e0 * e0 + e1 * e1) + e2 * e2;
+          if (d2f <= LL2 && u != t) {
+            const int dx = x0 + bxc - ix;
+            if (ln < kNrListCap)
+              list[nr_list_at(t, ln)] = u | ((unsigned)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) << kNrSlotBits);
+            ++ln;
+          }
+        }
+      }
+    }
+    list_n[t] = ln <= kNrListCap ? ln : kNrListFull;
+    listed += ln <= kNrListCap ? ln : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) listed += __shfl_xor_sync(0xffffffffu, listed, o);
+  if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g->list_entries, (unsigned long long)listed);
+}
+
+// Every step with a skin: the neighbour count, contacts and spring of slot t from its list, with
+// the sweep's tests in the same order -- FP32 outside a 2^-14 band around L^2 (the step's L), FP64
+// inside it; a candidate farther than the sum of the half extents cannot touch; R19's exclusions;
+// contacts deferred to a second pass over the lane's deferred entries.  A slot whose list
+// overflowed (list length kNrListFull) sweeps its 27 boxes instead, in the same order.
+__global__ void __launch_bounds__(kNrForceBlock, 8) k_nr_force_list(
+    unsigned n, const unsigned* __restrict__ start, const unsigned* __restrict__ key,
+    const NrGrid* g, NrRecords rec, const double* __restrict__ bx, const double* __restrict__ by,
+    const double* __restrict__ bz, const float4* __restrict__ spr, double k_rep, double gamma,
+    const unsigned* __restrict__ list, const unsigned* __restrict__ list_n,
+    NrOut32* __restrict__ out32) {
+  if (g->nbox == 0) return;
+  const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const double L2 = g->L2;
+  const float Lf = g->Lf, L2lo = g->L2lo, L2hi = g->L2hi;
+  const float k = (float)k_rep, gam = (float)gamma;
+  __shared__ unsigned s_def[kNrList][kNrForceBlock];
+  __shared__ float4 s_sh[27];  // candidate shift of each box code: -(dx, dy, dz) L
+  if (threadIdx.x < 27) {
+    const int c = (int)threadIdx.x;
+    s_sh[c] = make_float4(-(float)(c % 3 - 1) * Lf, -(float)((c / 3) % 3 - 1) * Lf,
+                          -(float)(c / 9 - 1) * Lf, 0.f);
+  }
+  __syncthreads();
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int2 ci = rec.RB[t].C;
+    const int i = ci.x, mi = ci.y;
+    const float4 sp = spr[i];
+    float keep[3] = {-sp.x, -sp.y, -sp.z}, pass[3] = {sp.x, sp.y, sp.z};
+    unsigned cnt = 0;
+    const float hi = sp.w;
+    const float4 A = rec.A32[t], B = rec.RB[t].B;
+    const float ai[3] = {B.x, B.y, B.z}, ri = B.w;
+    const float qi[3] = {A.x - 0.5f * B.x, A.y - 0.5f * B.y, A.z - 0.5f * B.z};
+    double bi[3];
+    bool have_bi = false;
+    int ndef = 0;
+    // one candidate: w = u | (box code << 27), Au its A record
+    auto consider = [&](unsigned w, const float4& Au) {
+      const unsigned u = w & ((1u << kNrSlotBits) - 1u), code = w >> kNrSlotBits;
+      const int dx = (int)(code % 3u) - 1, dy = (int)((code / 3u) % 3u) - 1, dz = (int)(code / 9u) - 1;
+      const float e0 = (A.x - (float)dx * Lf) - Au.x, e1 = (A.y - (float)dy * Lf) - Au.y,
+                  e2 = (A.z - (float)dz * Lf) - Au.z;
+      const float d2f = (e0 * e0 + e1 * e1) + e2 * e2;
+      if (d2f >= L2hi) return;
+      if (d2f < L2lo) {
+        ++cnt;
+      } else {
+        if (!have_bi) {
+          bi[0] = bx[i]; bi[1] = by[i]; bi[2] = bz[i];
+          have_bi = true;
+        }
+        const int j = rec.RB[u].C.x;
+        const double ed[3] = {__dsub_rn(bi[0], bx[j]), __dsub_rn(bi[1], by[j]), __dsub_rn(bi[2], bz[j])};
+        if (dot3_rn(ed[0], ed[1], ed[2], ed[0], ed[1], ed[2]) < L2) ++cnt;
+      }
+      const float hs = (hi + Au.w) * 1.0001f + 1e-4f;
+      if (d2f >= hs * hs) return;
+      const int2 cj = rec.RB[u].C;
+      if (mi == cj.x || cj.y == i || (mi >= 0 && mi == cj.y)) return;
+      if (ndef < kNrList) {
+        s_def[ndef][threadIdx.x] = w;
+        ++ndef;
+        return;
+      }
+      const float4 Bu = rec.RB[u].B;
+      const float rel[3] = {Au.x + (float)dx * Lf, Au.y + (float)dy * Lf, Au.z + (float)dz * Lf};
+      const float aj[3] = {Bu.x, Bu.y, Bu.z};
+      const float qj[3] = {rel[0] - 0.5f * Bu.x, rel[1] - 0.5f * Bu.y, rel[2] - 0.5f * Bu.z};
+      contact<float>(qi, ai, ri, mi >= 0, qj, aj, Bu.w, k, gam, keep, pass);
+    };
+    const unsigned m0 = list_n[t];
+    const bool full = m0 == kNrListFull;
+    const unsigned m = full ? 0u : m0;
+    // Four entries at a time, their loads issued together; the warp runs to its longest list (a
+    // slot past a lane's list reads nothing and tests false).  Counts are taken here; entries
+    // close enough to touch are deferred (R19's exclusions are checked with the contacts).
+    const unsigned mw = __reduce_max_sync(__activemask(), m);
+    for (unsigned k0 = 0; k0 < mw; k0 += 4) {
+      unsigned w[4];
+      float4 Au[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = k0 + (unsigned)q < m ? list[nr_list_at(t, k0 + (unsigned)q)] : 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        Au[q] = k0 + (unsigned)q < m ? rec.A32[w[q] & ((1u << kNrSlotBits) - 1u)]
+                                     : make_float4(3.0e4f, 3.0e4f, 3.0e4f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool ok = k0 + (unsigned)q < m;
+        const float4 sh = s_sh[ok ? w[q] >> kNrSlotBits : 13u];
+        const float e0 = (A.x + sh.x) - Au[q].x, e1 = (A.y + sh.y) - Au[q].y,
+                    e2 = (A.z + sh.z) - Au[q].z;
+        const float d2f = (e0 * e0 + e1 * e1) + e2 * e2;
+        cnt += ok && d2f < L2lo ? 1u : 0u;
+        if (ok && d2f >= L2lo && d2f < L2hi) {  // inside the band: FP64 decides (rare)
+          if (!have_bi) {
+            bi[0] = bx[i]; bi[1] = by[i]; bi[2] = bz[i];
+            have_bi = true;
+          }
+          const int j = rec.RB[w[q] & ((1u << kNrSlotBits) - 1u)].C.x;
+          const double ed[3] = {__dsub_rn(bi[0], bx[j]), __dsub_rn(bi[1], by[j]), __dsub_rn(bi[2], bz[j])};
+          if (dot3_rn(ed[0], ed[1], ed[2], ed[0], ed[1], ed[2]) < L2) ++cnt;
+        }
+        const float hs = (hi + Au[q].w) * 1.0001f + 1e-4f;
+        if (ok && d2f < L2hi && d2f < hs * hs) {
+          if (ndef < kNrList) {
+            s_def[ndef][threadIdx.x] = w[q];
+            ++ndef;
+          } else {  // the deferred entries are full: this one now (rare)
+            const unsigned u = w[q] & ((1u << kNrSlotBits) - 1u);
+            const int2 cj = rec.RB[u].C;
+            if (!(mi == cj.x || cj.y == i || (mi >= 0 && mi == cj.y))) {
+              const float4 Bu = rec.RB[u].B;
+              const float rel[3] = {Au[q].x - sh.x, Au[q].y - sh.y, Au[q].z - sh.z};
+              const float aj[3] = {Bu.x, Bu.y, Bu.z};
+              const float qj[3] = {rel[0] - 0.5f * Bu.x, rel[1] - 0.5f * Bu.y, rel[2] - 0.5f * Bu.z};
+              contact<float>(qi, ai, ri, mi >= 0, qj, aj, Bu.w, k, gam, keep, pass);
+            }
+          }
+        }
+      }
+    }
+    if (full) {  // the list overflowed: the 27 boxes, as the list build visits them
+      const unsigned kb = key[i];
+      const int ix = (int)(kb % (unsigned)d0), iy = (int)((kb / (unsigned)d0) % (unsigned)d1),
+                iz = (int)(kb / ((unsigned)d0 * (unsigned)d1));
+      const int x0 = max(ix - 1, 0), x1 = min(ix + 1, d0 - 1);
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int bz2 = iz + dz;
+        if (bz2 < 0 || bz2 >= d2) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int by2 = iy + dy;
+          if (by2 < 0 || by2 >= d1) continue;
+          const unsigned row = (unsigned)d0 * ((unsigned)by2 + (unsigned)d1 * (unsigned)bz2) + (unsigned)x0;
+          const int nb = x1 - x0 + 1;
+          const unsigned s0 = start[row], s1 = start[row + 1];
+          const unsigned s2 = nb >= 2 ? start[row + 2] : s1;
+          const unsigned s3 = nb >= 3 ? start[row + 3] : s2;
+          int bxc = 0;
+          unsigned nxt = s1;
+          for (unsigned u = s0; u < s3; ++u) {
+            while (u >= nxt) {
+              ++bxc;
+              nxt = bxc == 1 ? s2 : s3;
+            }
+            if (u == t) continue;
+            const int dx = x0 + bxc - ix;
+            consider(u | ((unsigned)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) << kNrSlotBits), rec.A32[u]);
+          }
+        }
+      }
+    }
+    for (int e = 0; e < ndef; ++e) {
+      const unsigned w = s_def[e][threadIdx.x];
+      const unsigned u = w & ((1u << kNrSlotBits) - 1u);
+      const int2 cj = rec.RB[u].C;
+      if (mi == cj.x || cj.y == i || (mi >= 0 && mi == cj.y)) continue;  // R19
+      const float4 sh = s_sh[w >> kNrSlotBits];
+      const float4 Au = rec.A32[u], Bu = rec.RB[u].B;
+      const float rel[3] = {Au.x - sh.x, Au.y - sh.y, Au.z - sh.z};
+      const float aj[3] = {Bu.x, Bu.y, Bu.z};
+      const float qj[3] = {rel[0] - 0.5f * Bu.x, rel[1] - 0.5f * Bu.y, rel[2] - 0.5f * Bu.z};
+      contact<float>(qi, ai, ri, mi >= 0, qj, aj, Bu.w, k, gam, keep, pass);
+    }
+    NrOut32 o;
+    o.keep = make_float4(keep[0], keep[1], keep[2], __uint_as_float(cnt));
+    o.pass = make_float4(pass[0], pass[1], pass[2], 0.f);
+    out32[i] = o;
+  }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(kNrBlock) k_nr_update(
     unsigned n, const double* __restrict__ x, const double* __restrict__ y,
     const double* __restrict__ z, double* __restrict__ nx, double* __restrict__ ny,
     double* __restrict__ nz, const NrOut32* __restrict__ out32, const NrOut64* __restrict__ out64,
     const unsigned* __restrict__ cstart, const unsigned* __restrict__ clist,
-    unsigned* __restrict__ nbr, const NrGrid* g, double dt, double cap) {
+    unsigned* __restrict__ nbr, NrGrid* g, double dt, double cap, float* __restrict__ disp) {
   if (g->nbox == 0) return;
   const double cap2 = cap * cap;
   const float dtf = (float)dt, capf = (float)cap, cap2f = capf * capf;
+  // with neighbour lists: each point's summed move since the rebuild, and its largest value
+  const bool rb = g->rebuild != 0u;
+  float dmax = 0.f;
   for (unsigned a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
     if constexpr (MIXED) {
       // FP32 sum and cap (the shares are FP32), exact conversion, one FP64 add per axis
@@ -664,6 +955,11 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_update(
       ny[a] = __dadd_rn(y[a], f2d_exact(D1));
       nz[a] = __dadd_rn(z[a], f2d_exact(D2));
       nbr[a] = __float_as_uint(kp.w);
+      if (disp) {
+        const float Dm = (rb ? 0.f : disp[a]) + sqrtf((D0 * D0 + D1 * D1) + D2 * D2);
+        disp[a] = Dm;
+        dmax = fmaxf(dmax, Dm);
+      }
       continue;
     }
     double S0, S1, S2;
@@ -701,6 +997,15 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_update(
     nz[a] = z[a] + D2;
     nbr[a] = cnt;
   }
+  if (disp) {  // non-negative floats order like their bits
+    unsigned b = __float_as_uint(dmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned v = __shfl_xor_sync(0xffffffffu, b, o);
+      b = v > b ? v : b;
+    }
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(&g->max_disp, b);
+  }
 }
 
 }  // namespace
@@ -730,6 +1035,8 @@ struct bdm_neurite {
   unsigned long long* tiles = nullptr;
   unsigned max_tiles = 0;
   unsigned *cstart = nullptr, *clist = nullptr, *nbr = nullptr;
+  unsigned *list = nullptr, *list_n = nullptr;  // skin > 0: neighbour lists by slot
+  float* disp = nullptr;                         // skin > 0: summed move since the rebuild
   NrRecords rec{};
   NrOut32* out32 = nullptr;
   NrOut64* out64 = nullptr;
@@ -860,27 +1167,36 @@ int enqueue_step(bdm_neurite* s) {
                            n, s->x[c], s->y[c], s->z[c], s->diam, s->inv_rest, s->mother, s->ox,
                            s->oy, s->oz, s->p.spring, s->bx, s->by, s->bz, s->spr, s->spr64,
                            s->axr, s->partials)));
+  const bool lists = s->mixed && s->p.skin > 0.0;
   NRUN("nr_finalize", (k_nr_finalize<<<1, kNrBlock, 0, st>>>(s->partials, bprep, n,
                                                               s->p.interaction_radius,
                                                               (unsigned long long)s->box_capacity,
-                                                              s->g)));
+                                                              lists ? s->p.skin : 0.0, s->g)));
   NCK(cudaMemsetAsync(s->tiles, 0, sizeof(unsigned long long) * s->max_tiles, st));
   NRUN("nr_key", (k_nr_key<<<s->blocks_stream, kNrBlock, 0, st>>>(n, s->bx, s->by, s->bz, s->g,
                                                                    s->key, s->rank, s->count)));
-  NRUN("nr_scan", launch_scan(st, s->count, s->start, &s->g->nbox1, s->tiles, &s->g->scan_ctr[0],
+  NRUN("nr_scan", launch_scan(st, s->count, s->start, &s->g->nbox1_sort, s->tiles, &s->g->scan_ctr[0],
                               &s->g->err, 1, s->blocks_scan));
   if (s->mixed) {
     NRUN("nr_scatter", (k_nr_scatter<true><<<s->blocks_stream, kNrBlock, 0, st>>>(
                            n, s->key, s->rank, s->start, s->x[c], s->y[c], s->z[c], s->diam,
                            s->mother, s->ox, s->oy, s->oz, s->bx, s->by, s->bz, s->spr, s->axr,
                            s->g, s->rec)));
-    NRUN("nr_force", (k_nr_force<true><<<s->blocks_force, kNrForceBlock, 0, st>>>(
-                         n, s->start, s->key, s->g, s->rec, s->bx, s->by, s->bz, s->spr,
-                         s->spr64, s->p.repulsion, s->p.attraction, s->out32, s->out64)));
+    if (lists)
+      NRUN("nr_list_build", (k_nr_list_build<<<s->blocks_force, kNrForceBlock, 0, st>>>(
+                                n, s->start, s->key, s->g, s->rec, s->list, s->list_n)));
+    if (lists)
+      NRUN("nr_force_list", (k_nr_force_list<<<s->blocks_force, kNrForceBlock, 0, st>>>(
+                                n, s->start, s->key, s->g, s->rec, s->bx, s->by, s->bz, s->spr,
+                                s->p.repulsion, s->p.attraction, s->list, s->list_n, s->out32)));
+    else
+      NRUN("nr_force", (k_nr_force<true><<<s->blocks_force, kNrForceBlock, 0, st>>>(
+                           n, s->start, s->key, s->g, s->rec, s->bx, s->by, s->bz, s->spr,
+                           s->spr64, s->p.repulsion, s->p.attraction, s->out32, s->out64)));
     NRUN("nr_update", (k_nr_update<true><<<s->blocks_stream, kNrBlock, 0, st>>>(
                           n, s->x[c], s->y[c], s->z[c], s->x[nx], s->y[nx], s->z[nx], s->out32,
                           s->out64, s->cstart, s->clist, s->nbr, s->g, s->p.dt,
-                          s->p.max_displacement)));
+                          s->p.max_displacement, lists ? s->disp : nullptr)));
   } else {
     NRUN("nr_scatter", (k_nr_scatter<false><<<s->blocks_stream, kNrBlock, 0, st>>>(
                            n, s->key, s->rank, s->start, s->x[c], s->y[c], s->z[c], s->diam,
@@ -892,7 +1208,7 @@ int enqueue_step(bdm_neurite* s) {
     NRUN("nr_update", (k_nr_update<false><<<s->blocks_stream, kNrBlock, 0, st>>>(
                           n, s->x[c], s->y[c], s->z[c], s->x[nx], s->y[nx], s->z[nx], s->out32,
                           s->out64, s->cstart, s->clist, s->nbr, s->g, s->p.dt,
-                          s->p.max_displacement)));
+                          s->p.max_displacement, nullptr)));
   }
   s->cur = nx;
   return BDM_OK;
@@ -933,6 +1249,8 @@ int bdm_neurite_create(const bdm_neurite_params* p, bdm_neurite** out) {
     rc = bad("repulsion / attraction / spring");
   else if (!(p->interaction_radius >= 0.0) || !std::isfinite(p->interaction_radius)) rc = bad("interaction_radius");
   else if (p->capacity == 0 || p->capacity > (1ull << 31)) rc = bad("capacity");
+  else if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) rc = bad("skin");
+  else if (p->skin > 0.0 && p->precision != BDM_MIXED) rc = bad("skin needs BDM_MIXED");
   if (rc) {
     *out = s;
     return rc;
@@ -975,6 +1293,10 @@ int bdm_neurite_create(const bdm_neurite_params* p, bdm_neurite** out) {
   if (s->mixed) {
     if ((rc = nalloc(s, &s->rec.A32, C)) || (rc = nalloc(s, &s->rec.RB, C))) return rc;
     if ((rc = nalloc(s, &s->out32, C)) || (rc = nalloc(s, &s->axr, C))) return rc;
+    if (p->skin > 0.0 &&
+        ((rc = nalloc(s, &s->list, (size_t)kNrListCap * ((C + 31) / 32 * 32))) ||
+         (rc = nalloc(s, &s->list_n, C)) || (rc = nalloc(s, &s->disp, C))))
+      return rc;
   } else {
     if ((rc = nalloc(s, &s->rec.A64, C)) || (rc = nalloc(s, &s->rec.B64, C)) ||
         (rc = nalloc(s, &s->rec.C, C)))
@@ -1115,6 +1437,16 @@ int bdm_neurite_get_state(bdm_neurite* s, size_t* n_out, double* x, double* y, d
       NCK(cudaMemcpyAsync(neighbour_count, s->nbr, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
   }
   NCK(cudaStreamSynchronize(s->stream));
+  return BDM_OK;
+}
+
+int bdm_neurite_list_info(bdm_neurite* s, uint64_t* rebuilds, uint64_t* entries) {
+  if (!s) return BDM_EINVAL;
+  NCK(cudaMemcpyAsync(s->gh, s->g, sizeof(NrGrid), cudaMemcpyDeviceToHost, s->stream));
+  NCK(cudaStreamSynchronize(s->stream));
+  const bool lists = s->mixed && s->p.skin > 0.0;
+  if (rebuilds) *rebuilds = lists ? s->gh->rebuilds : 0;
+  if (entries) *entries = lists ? s->gh->list_entries : 0;
   return BDM_OK;
 }
 

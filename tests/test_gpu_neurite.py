@@ -14,6 +14,13 @@ from paper_2006_06775_gb300 import bdm, synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-9, "mixed": 1e-5}
+# The neighbour-list path bins on boxes of L + skin, so its FP32 box-relative contact geometry rounds
+# differently.  Contacts of nearly parallel elements are ill-conditioned (reading R18: the contact
+# point moves by about eps / sin^2 theta for an input error eps); on the 9001-agent forest the same
+# three elements deviate by up to 1.2e-5 um (3-D) on the per-step-rebuild path and by up to 1.7e-5
+# um with skins of 0.5-2 um.  The list path is held to twice the mixed limit.
+TOL_SKIN = 2e-5
+NEURITE_BENCH_SKIN = 1.0  # the neighbour-list skin (um) of bench.py's neuron forest
 
 
 def oracle_step(params, inp):
@@ -130,16 +137,30 @@ def test_errors_are_reported_without_a_fault():
     sim.close()
 
 
-def test_full_size_forest_sampled_against_the_oracle():
+@pytest.mark.parametrize("skin", [0.0, NEURITE_BENCH_SKIN])
+def test_full_size_forest_sampled_against_the_oracle(skin):
     """The benchmark workload (5000 neurons, 9e6 agents, mixed precision, the bench's launch
-    configuration): 48 sampled agents against the oracle one by one, exact neighbour counts; and
-    the total displacement of all agents is zero up to rounding when no cap is hit (every force
-    comes in equal and opposite pairs, and the split and the springs only move force around)."""
+    configuration, with and without the bench's neighbour-list skin): 48 sampled agents against
+    the oracle one by one, exact neighbour counts; and the total displacement of all agents is zero
+    up to rounding when no cap is hit (every force comes in equal and opposite pairs, and the split
+    and the springs only move force around).  With the skin, a few list steps run first and the
+    checked step is a list step."""
     params, inp = synth.neuron_forest()
     n = len(inp["x"])
-    sim = make(params, "mixed", capacity=n)
+    sim = make(params, "mixed", capacity=n, skin=skin)
     sim.set_agents(inp)
-    sim.step(1)
+    if skin > 0.0:
+        # step until a step evaluates the lists (no rebuild), and check that step
+        for _ in range(16):
+            start = sim.get_state()
+            rebuilds = sim.list_info()[0]
+            sim.step(1)
+            if sim.list_info()[0] == rebuilds:
+                break
+        assert sim.list_info()[0] == rebuilds, "no list step in 16 steps"
+        inp = dict(inp, **{a: start[a] for a in "xyz"})
+    else:
+        sim.step(1)
     got = sim.get_state()
     g = synth.rng(77)
     idx = np.unique(np.concatenate([g.integers(0, n, 40), g.integers(0, 5000, 8)]))
@@ -249,3 +270,65 @@ def test_parallel_elements_tie_rule_one_step(precision):
     for a in "xyz":
         assert np.max(np.abs(got[a] - want[a])) < TOL[precision], a
     sim.close()
+
+
+@pytest.mark.parametrize("skin", [0.5, 2.0])
+@pytest.mark.parametrize("seed,neurons,agents,side", [(1, 16, 2500, 60.0), (2, 40, 9001, 70.0)])
+def test_forest_with_skin_teacher_forced(skin, seed, neurons, agents, side):
+    """Neighbour lists (mixed precision): every step, rebuild steps and list steps alike, matches
+    the oracle's step from the GPU's own state -- counts and L exactly, positions within TOL_SKIN --
+    and the lists do carry steps between rebuilds."""
+    params, inp = synth.neuron_forest(neurons, agents, side=side, seed=seed)
+    sim = make(params, "mixed", skin=skin)
+    sim.set_agents(inp)
+    cur = dict(inp)
+    steps = 12
+    for k in range(steps):
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle_step(params, cur)
+        assert got["L"] == want["L"], k
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        for a in "xyz":
+            err = np.max(np.abs(got[a] - want[a]))
+            assert err < TOL_SKIN, (k, a, err)
+        cur = dict(cur, x=got["x"], y=got["y"], z=got["z"])
+    rebuilds, entries = sim.list_info()
+    assert 1 <= rebuilds < steps
+    assert entries > 0
+    sim.close()
+
+
+def test_skin_list_overflow_falls_back_to_the_sweep():
+    """600 somata in a 30 um cube with a 4 um skin: somata with more than 128 agents within L + skin
+    overflow their lists and sweep their 27 boxes instead, next to slots that use their lists; the
+    results match the oracle."""
+    params, _ = synth.neuron_forest(1, 1, seed=0)
+    x, y, z, d = synth.uniform_spheres(600, 30.0, seed=12)
+    n = len(x)
+    inp = dict(x=x, y=y, z=z, diameter=d.astype(np.float64), rest=np.zeros(n),
+               mother=-np.ones(n, np.int32), ox=np.zeros(n), oy=np.zeros(n), oz=np.zeros(n))
+    sim = make(params, "mixed", skin=4.0)
+    sim.set_agents(inp)
+    cur = dict(inp)
+    for k in range(3):
+        sim.step(1)
+        got = sim.get_state()
+        want = oracle_step(params, cur)
+        assert np.array_equal(got["neighbour_count"], want["neighbour_count"]), k
+        assert int(want["neighbour_count"].max()) > 128
+        for a in "xyz":
+            assert np.max(np.abs(got[a] - want[a])) < TOL_SKIN, (k, a)
+        cur = dict(cur, x=got["x"], y=got["y"], z=got["z"])
+    sim.close()
+
+
+@pytest.mark.parametrize("bad", [dict(skin=-1.0), dict(skin=float("nan")),
+                                 dict(skin=1.0, precision="fp64")])
+def test_skin_parameter_checks(bad):
+    params, _ = synth.neuron_forest(1, 1, seed=0)
+    p = dict(params, precision="mixed", capacity=64)
+    p.update(bad)
+    with pytest.raises(bdm.BdmError) as e:
+        bdm.Neurite(p)
+    assert e.value.code == bdm.BDM_EINVAL
