@@ -205,6 +205,23 @@ __device__ __forceinline__ void contact(const T qi[3], const T ai[3], T ri, bool
   }
 }
 
+// mixed records of one box-ordered slot: A = (binning point - box corner, half extent bound) in a
+// dense array (the sweep reads only A), and one 32 B sector holding B = (axis p - q, radius) and the
+// (id, mother) pair, which only contacts and exclusions read
+struct alignas(32) NrRecB {
+  float4 B;
+  int2 C;
+  int2 pad;
+};
+
+struct NrRecords {
+  Dbl4* A64;     // FP64: (q, r)
+  Dbl4* B64;     // FP64: (p, half extent bound)
+  float4* A32;   // mixed: A records
+  NrRecB* RB;    // mixed: B + (id, mother) records
+  int2* C;       // FP64: (id, mother)
+};
+
 // ---- per-step kernels ---------------------------------------------------------------------------
 // GB300's FP64 pipe is narrow: the streaming kernels keep FP64 to what the exact results need
 // (proximal and binning points, lengths -- they decide L and the neighbour counts -- and the
@@ -219,7 +236,13 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_prepare(
     const double* __restrict__ ox, const double* __restrict__ oy, const double* __restrict__ oz,
     double k_spring, double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
     float4* __restrict__ spr, Dbl4* __restrict__ spr64, float4* __restrict__ axr,
-    double* __restrict__ partials) {
+    double* __restrict__ partials, const NrGrid* g, const unsigned* __restrict__ key,
+    const unsigned* __restrict__ rank, const unsigned* __restrict__ start, NrRecords rec) {
+  // with neighbour lists (rec.A32 given) the records also go straight into the slots of the last
+  // rebuild: a list step then needs no scatter, and a rebuild step's scatter overwrites them
+  const bool direct = MIXED && rec.A32 != nullptr && g->nbox != 0 && g->list_valid;
+  const int gd0 = g->dims[0], gd1 = g->dims[1];
+  const double Lbox = g->Lbox;
   // bounds in the order-preserving integer encoding of doubles (integer compares; GB300's FP64
   // pipe is narrow)
   unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull}, ext = 0ull;
@@ -261,8 +284,22 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_prepare(
     by[a] = b[1];
     bz[a] = b[2];
     spr[a] = f;
-    if constexpr (MIXED) axr[a] = make_float4((float)ax, (float)ay, (float)az, (float)(0.5 * d));
-    else spr64[a] = f64;
+    if constexpr (MIXED) {
+      const float4 B = make_float4((float)ax, (float)ay, (float)az, (float)(0.5 * d));
+      axr[a] = B;
+      if (direct) {  // as k_nr_scatter computes them, in the rebuild's slot and box
+        const unsigned k = key[a];
+        const unsigned slot = start[k] + rank[a];
+        const unsigned ix = k % (unsigned)gd0, iy = (k / (unsigned)gd0) % (unsigned)gd1,
+                       iz = k / ((unsigned)gd0 * (unsigned)gd1);
+        rec.A32[slot] = make_float4((float)(b[0] - (g->origin[0] + (double)ix * Lbox)),
+                                    (float)(b[1] - (g->origin[1] + (double)iy * Lbox)),
+                                    (float)(b[2] - (g->origin[2] + (double)iz * Lbox)), f.w);
+        rec.RB[slot].B = B;
+      }
+    } else {
+      spr64[a] = f64;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const unsigned long long eb = enc_double(b[c]);
@@ -426,23 +463,6 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_key(unsigned n, const double* _
   }
 }
 
-// mixed records of one box-ordered slot: A = (binning point - box corner, half extent bound) in a
-// dense array (the sweep reads only A), and one 32 B sector holding B = (axis p - q, radius) and the
-// (id, mother) pair, which only contacts and exclusions read
-struct alignas(32) NrRecB {
-  float4 B;
-  int2 C;
-  int2 pad;
-};
-
-struct NrRecords {
-  Dbl4* A64;     // FP64: (q, r)
-  Dbl4* B64;     // FP64: (p, half extent bound)
-  float4* A32;   // mixed: A records
-  NrRecB* RB;    // mixed: B + (id, mother) records
-  int2* C;       // FP64: (id, mother)
-};
-
 // (id, mother) of a box-ordered slot
 template <bool MIXED>
 __device__ __forceinline__ int2 rec_c(const NrRecords& rec, unsigned u) {
@@ -458,8 +478,9 @@ __global__ void __launch_bounds__(kNrBlock) k_nr_scatter(
     const double* __restrict__ ox, const double* __restrict__ oy, const double* __restrict__ oz,
     const double* __restrict__ bx, const double* __restrict__ by, const double* __restrict__ bz,
     const float4* __restrict__ spr, const float4* __restrict__ axr, const NrGrid* g,
-    NrRecords rec) {
-  if (g->nbox == 0) return;
+    NrRecords rec, int lists) {
+  // with neighbour lists a list step's records were written by k_nr_prepare
+  if (g->nbox == 0 || (lists && !g->rebuild)) return;
   const int d0 = g->dims[0], d1 = g->dims[1];
   const double Lbox = g->Lbox;
   for (unsigned a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
@@ -1161,12 +1182,13 @@ int enqueue_step(bdm_neurite* s) {
     NRUN("nr_prepare", (k_nr_prepare<true><<<bprep, kNrBlock, 0, st>>>(
                            n, s->x[c], s->y[c], s->z[c], s->diam, s->inv_rest, s->mother, s->ox,
                            s->oy, s->oz, s->p.spring, s->bx, s->by, s->bz, s->spr, s->spr64,
-                           s->axr, s->partials)));
+                           s->axr, s->partials, s->g, s->key, s->rank, s->start,
+                           s->p.skin > 0.0 ? s->rec : NrRecords{})));
   else
     NRUN("nr_prepare", (k_nr_prepare<false><<<bprep, kNrBlock, 0, st>>>(
                            n, s->x[c], s->y[c], s->z[c], s->diam, s->inv_rest, s->mother, s->ox,
                            s->oy, s->oz, s->p.spring, s->bx, s->by, s->bz, s->spr, s->spr64,
-                           s->axr, s->partials)));
+                           s->axr, s->partials, s->g, s->key, s->rank, s->start, NrRecords{})));
   const bool lists = s->mixed && s->p.skin > 0.0;
   NRUN("nr_finalize", (k_nr_finalize<<<1, kNrBlock, 0, st>>>(s->partials, bprep, n,
                                                               s->p.interaction_radius,
@@ -1181,7 +1203,7 @@ int enqueue_step(bdm_neurite* s) {
     NRUN("nr_scatter", (k_nr_scatter<true><<<s->blocks_stream, kNrBlock, 0, st>>>(
                            n, s->key, s->rank, s->start, s->x[c], s->y[c], s->z[c], s->diam,
                            s->mother, s->ox, s->oy, s->oz, s->bx, s->by, s->bz, s->spr, s->axr,
-                           s->g, s->rec)));
+                           s->g, s->rec, lists ? 1 : 0)));
     if (lists)
       NRUN("nr_list_build", (k_nr_list_build<<<s->blocks_force, kNrForceBlock, 0, st>>>(
                                 n, s->start, s->key, s->g, s->rec, s->list, s->list_n)));
@@ -1201,7 +1223,7 @@ int enqueue_step(bdm_neurite* s) {
     NRUN("nr_scatter", (k_nr_scatter<false><<<s->blocks_stream, kNrBlock, 0, st>>>(
                            n, s->key, s->rank, s->start, s->x[c], s->y[c], s->z[c], s->diam,
                            s->mother, s->ox, s->oy, s->oz, s->bx, s->by, s->bz, s->spr, s->axr,
-                           s->g, s->rec)));
+                           s->g, s->rec, lists ? 1 : 0)));
     NRUN("nr_force", (k_nr_force<false><<<s->blocks_force, kNrForceBlock, 0, st>>>(
                          n, s->start, s->key, s->g, s->rec, s->bx, s->by, s->bz, s->spr,
                          s->spr64, s->p.repulsion, s->p.attraction, s->out32, s->out64)));
