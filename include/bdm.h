@@ -74,7 +74,9 @@ typedef struct bdm_params {
                                     are listed only when some agent has moved more than skin / 2
                                     since the last rebuild (or after 64 steps); the steps between
                                     evaluate the lists.  Integer state stays exact every step; the
-                                    FP32 force sums follow the order of the last rebuild.          */
+                                    FP32 force sums follow the order of the last rebuild.  A tiny
+                                    skin (e.g. 0.001 um) rebuilds every step through the list
+                                    kernels, faster than skin 0's walk at 1e7-1e8 agents.          */
   /* Growth and division (reading R7). */
   int32_t growth_enabled;
   int32_t force_variant;         /* mixed force kernel: 0 = one thread per agent, 1 = warp-shared
